@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: fused-gate state-vector simulation of a 30-qubit random grid circuit.
+
+Workload (default): 30 qubits on a 5 x 6 grid, 24 cycles of {sqrtX, sqrtY, sqrtW} on
+every qubit + fSim(pi/2, pi/6) on one of four edge classes (720 + 294 = 1014 gates),
+seeded; complex64 state (8 GiB, larger than L2), DAG fusion at k = 5, adaptive
+c64 -> c128 promotion on norm drift > 1e-6.  One step is the whole hot path:
+  sv_fuse (host DAG fusion) -> sv_set_basis -> sv_apply_circuit (FP64 norm before and
+  after, every fused pass) -> sv_topk(64) -> sv_expect(<Z0 Z1>).
+Metric: circuits/s (whole job), with the fused-gate HBM GB/s of the apply kernels.
+
+--impl reference times the CPU oracle (complex128, unfused, OpenMP over the host cores)
+on bounded samples of the same workload, scaled to circuits/s.
+Under torchrun each rank runs an independent replica (no collective on the data path).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = ("fused-gate HBM GB/s & circuits/s at 28–33q vs unfused c128; "
+          "served p50/p99 latency")
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic of one apply pass at 30 qubits complex64, fused width 5, from the ncu
+# capture summarised in profiles/apply_tile_c64_30q.md; valid only for the kernel source
+# with this sha256 prefix (null otherwise).
+TRAFFIC = {"sha256_prefix": None, "bytes_per_launch": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--cycles", type=int, default=24)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare-unfused", action="store_true",
+                    help="also time the unfused complex128 per-gate form once")
+    ap.add_argument("--cpu-sample-s", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("apply_kernels.cu", "ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2604_03816_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    mx.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(specs, n, budget_s, gates_total):
+    """The oracle (complex128, unfused, OpenMP) on a bounded sample: as many of the
+    workload's gates as fit in about budget_s seconds at full width."""
+    import oracle
+    from oracle import gates as OG
+    gl = OG.gate_list(specs)
+    psi = oracle.basis(n, 0)
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(gl) and (done < 2 or time.perf_counter() - t0 < budget_s):
+        oracle.apply_gate(psi, *gl[done])
+        done += 1
+    dt = time.perf_counter() - t0
+    del psi
+    per_gate = dt / done
+    return {"value": 1.0 / (per_gate * gates_total), "unit": "circuits/s",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {done} of {gates_total} gates of the {n}-qubit workload, "
+                      f"complex128 unfused, {dt:.1f} s, scaled to one circuit"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    from oracle import gates as OG
+    specs = W.grid_random(args.n, args.cycles)
+    gl = OG.gate_list(specs)
+    psi = oracle.basis(args.n, 0)
+    per_step = max(1, int(os.environ.get("REF_GATES_PER_STEP", "3")))
+    times = []
+    pos = 0
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for _ in range(per_step):
+            oracle.apply_gate(psi, *gl[pos % len(gl)])
+            pos += 1
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = args.steps * per_step / total / len(gl)
+    cores = oracle.num_threads()
+    out = {"metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": config_dict(args, len(specs), None),
+           "cpu_baseline": {"value": value, "unit": "circuits/s", "cores": cores,
+                            "kind": "oracle",
+                            "sample": f"{per_step} gates per step of the {args.n}-qubit "
+                                      f"workload (complex128, unfused), scaled to circuits"},
+           "e2e": {"value": value, "unit": "circuits/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(args, ngates, nfused):
+    return {"workload": f"grid_random {args.n}q depth {args.cycles} "
+                        f"({'sqrtX/sqrtY/sqrtW + fSim(pi/2,pi/6)'}), {args.dtype}, "
+                        f"DAG fusion k={args.k}, adaptive c64->c128 at drift 1e-6",
+            "n_qubits": args.n, "gates": ngates, "fused_gates": nfused, "max_k": args.k,
+            "state_dtype": args.dtype, "state_bytes": (8 if args.dtype == "c64" else 16) << args.n,
+            "l2": "state larger than L2 (inputs > 129 MB), no flush needed",
+            "seed": W.seed_for(3, args.n)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_info()
+    import torch
+    from paper_2604_03816_gb300 import sv
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    dt = sv.SV_C64 if args.dtype == "c64" else sv.SV_C128
+    specs = W.grid_random(args.n, args.cycles)
+    gates = sv.gates_from_specs(specs)          # gate construction: once, host
+    ga = sv.GateArray(gates)
+    state = sv.sv_alloc(args.n, dt, stream=stream)
+    launches_per_step = [0]
+
+    def step(timing=False):
+        c = sv.sv_fuse(gates, args.n, args.k)
+        sv.sv_set_basis(state, 0)
+        rep = sv.sv_apply_circuit(state, c, adaptive=True, timing=timing)
+        idx, p = sv.sv_topk(state, 64)
+        zz = sv.sv_expect(state, [0], [3], [1.0])
+        # kernels: passes + 2 x norm (2 each) + set_basis (1) + top-k (2) + expect (2)
+        launches_per_step[0] = rep["passes"] + 4 * (1 + rep["promotions"]) + 1 + 2 + 2
+        return rep, len(c), (idx, p, zz)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            rep, nfused, _ = step()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(local).uuid)
+            uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = []
+        with ClockSampler(uuid) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                reps.append(step(timing=True)[0])
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        clocks = clk.summary()
+
+        # dominant kernel: the apply passes, timed with CUDA events on the state's stream
+        apply_ms = sum(r["apply_ms"] for r in reps)
+        apply_bytes = sum(r["bytes"] for r in reps)
+        passes = sum(r["passes"] for r in reps)
+        achieved = apply_bytes / (apply_ms / 1000.0) / 1e9
+        peak, peak_kind = hbm_peak()
+        sha = kernel_sha()
+        traffic = None
+        if TRAFFIC["sha256_prefix"] and sha.startswith(TRAFFIC["sha256_prefix"]):
+            traffic = TRAFFIC["bytes_per_launch"]
+
+        if sv.sv_info(state)[1] != dt:          # a promotion widened the state: start over
+            state.free()
+            state = sv.sv_alloc(args.n, dt, stream=stream)
+        # end to end through the C ABI with host buffers: the initial state in from pinned
+        # host memory, all 2^n probabilities out to pinned host memory, every step
+        e2e = None
+        if args.e2e_steps > 0:
+            npdt = np.complex64 if dt == sv.SV_C64 else np.complex128
+            h_in = torch.zeros(1 << args.n, dtype=torch.complex64 if dt == sv.SV_C64
+                               else torch.complex128).pin_memory()
+            h_in[0] = 1.0
+            h_out = torch.empty(1 << args.n, dtype=torch.float32 if dt == sv.SV_C64
+                                else torch.float64).pin_memory()
+            h_in_np, h_out_np = h_in.numpy(), h_out.numpy()
+            assert h_in_np.dtype == npdt
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.e2e_steps):
+                sv.sv_set_state(state, h_in_np)
+                c = sv.sv_fuse(gates, args.n, args.k)
+                sv.sv_apply_circuit(state, c, adaptive=True)
+                sv.sv_probs(state, h_out_np)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms = f0.elapsed_time(f1)
+            e2e = {"value": world * args.e2e_steps / (e2e_ms / 1000.0), "unit": "circuits/s",
+                   "h2d_bytes_per_step": int(h_in_np.nbytes),
+                   "d2h_bytes_per_step": int(h_out_np.nbytes),
+                   "steps": args.e2e_steps,
+                   "includes": "sv_set_state(host pinned) + sv_fuse + sv_apply_circuit + "
+                               "sv_probs(host pinned)"}
+            del h_in, h_out
+
+        unfused = None
+        if args.compare_unfused:
+            s128 = sv.sv_alloc(args.n, sv.SV_C128, stream=stream)
+            cu = sv.sv_fuse(gates, args.n, 0)
+            r = sv.sv_apply_circuit(s128, cu, timing=True)
+            unfused = {"circuits_per_s": 1000.0 / r["apply_ms"], "passes": r["passes"],
+                       "apply_ms": r["apply_ms"],
+                       "effective_gbs": r["bytes"] / (r["apply_ms"] / 1000.0) / 1e9}
+            s128.free()
+
+    state.free()
+    if rank != 0:
+        return
+    value = world * args.steps / (ms / 1000.0)
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_baseline(specs, args.n, args.cpu_sample_s, len(specs))
+    out = {"metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if dt == sv.SV_C64 else "f64", "data": "synthetic",
+           "config": config_dict(args, len(specs), nfused),
+           "fused_gate_hbm_gbs": achieved,
+           "promotions": sum(r["promotions"] for r in reps),
+           "max_drift": max(r["drift"] for r in reps),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": traffic,
+                        "kernel": "apply_tile (fused-gate pass)", "peak_kind": peak_kind,
+                        "algorithmic_bytes_per_launch": apply_bytes / passes,
+                        "avg_launch_ms": apply_ms / passes},
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step[0] * args.steps,
+           "clocks": clocks}
+    if unfused:
+        out["unfused_c128"] = unfused
+        out["speedup_vs_unfused_c128"] = value / unfused["circuits_per_s"]
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * sv.h -- C ABI of the GB300 state-vector simulator core.
+ *
+ * The library applies a circuit's gates, after DAG gate fusion has merged runs of gates
+ * into dense k-qubit unitaries (k <= 5), to the 2^n complex amplitudes of |psi> on one
+ * GPU, and computes the norm, Z-basis probability, Pauli-expectation and top-k
+ * reductions.  It follows the paper's statement of the problem:
+ *   - a gate is a unitary U_g in C^{2^q x 2^q} plus a tuple of targets (Section 3);
+ *   - the pipeline is |psi_out> = E(R(F(P(C)))) (Eq. 5): F = sv_fuse (Section 5.2,
+ *     Algorithm 2), R = the precision choice (Eqs. 11-12 plus runtime norm drift),
+ *     E = sv_apply_circuit on the GPU;
+ *   - a backend offers initialisation, gate application and measurement (Section 4.1):
+ *     sv_alloc / sv_set_basis, sv_apply_circuit / sv_apply_gate, sv_probs / sv_expect /
+ *     sv_topk / sv_norm.
+ *
+ * Conventions
+ *   - Qubit t is bit t of the amplitude index (little-endian), as fixed by Eq. 3:
+ *     (I_{2^{n-t-1}} (x) U (x) I_{2^t}) puts qubit t at stride 2^t.
+ *   - Amplitudes are interleaved (re, im): SV_C64 = two floats (8 bytes per amplitude),
+ *     SV_C128 = two doubles (16 bytes per amplitude), Eq. 1 / Section 5.4.
+ *   - Gate matrices are 2^k x 2^k, row-major, interleaved (re, im) doubles; local index
+ *     bit j of the matrix belongs to targets[j].
+ *
+ * Errors: every call validates its arguments and returns an sv_status; nothing aborts
+ * or throws across the ABI.  sv_last_error() returns the calling thread's last message.
+ * GPU work is enqueued on the state's stream; calls that return host values (sv_norm,
+ * sv_expect, sv_topk, sv_get_state to host, ...) synchronise that stream.  Device-side
+ * bounded waits that give up set an error word that the next synchronising call reports
+ * as SV_ERR_TIMEOUT.
+ *
+ * Threading: a state or circuit may be used by one thread at a time; different states
+ * may be driven from different threads (each on its own stream).
+ */
+#ifndef SV_GB300_H
+#define SV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = 1,      /* invalid argument (message in sv_last_error) */
+    SV_ERR_OOM = 2,      /* device or host allocation failed */
+    SV_ERR_CUDA = 3,     /* a CUDA runtime call failed */
+    SV_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    SV_ERR_STATE = 5     /* the operation does not fit the state (e.g. buffer too small) */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+#define SV_MAX_K 5         /* widest gate the kernels apply (fused width k <= 5) */
+#define SV_MAX_QUBITS 34   /* 2^34 amplitudes */
+
+typedef struct sv_state sv_state;       /* opaque: a device state vector + workspace */
+typedef struct sv_circuit sv_circuit;   /* opaque: a fused schedule, host memory */
+
+/* One gate (Section 3): k targets, distinct, each < n; u = 2^k x 2^k complex matrix,
+ * row-major interleaved doubles, local bit j <-> targets[j].  Caller owns u. */
+typedef struct {
+    uint32_t k;
+    uint32_t targets[SV_MAX_K];
+    const double *u;
+} sv_gate;
+
+/* ------------------------------------------------------------------ gate library */
+
+/* The canonical gate set G of Eq. 4 plus the full-unitary gates the workloads use. */
+typedef enum {
+    SV_GATE_I = 0, SV_GATE_X, SV_GATE_Y, SV_GATE_Z, SV_GATE_H, SV_GATE_S, SV_GATE_T,
+    SV_GATE_RX, SV_GATE_RY, SV_GATE_RZ,           /* R_a(theta) = exp(-i theta A / 2) */
+    SV_GATE_CNOT, SV_GATE_CZ, SV_GATE_SWAP, SV_GATE_TOFFOLI,
+    SV_GATE_U3,                                   /* U3(theta, phi, lambda), OpenQASM 2 form */
+    SV_GATE_SQRTX, SV_GATE_SQRTY, SV_GATE_SQRTW,  /* ((1+i) I + (1-i) P) / 2 */
+    SV_GATE_FSIM,                                 /* fSim(theta, phi) */
+    SV_GATE_CP,                                   /* diag(1, 1, 1, e^{i phi}) */
+    SV_GATE_UNITARY                               /* params = the matrix itself */
+} sv_gate_kind;
+
+/* Matrix of a gate of the canonical set (Eq. 4).  params: angles (RX/RY/RZ/CP: 1,
+ * U3: 3, FSIM: 2, others: 0); for SV_GATE_UNITARY params is the 2^k x 2^k interleaved
+ * matrix and nparams = 2 * 4^k.  dagger != 0 returns the adjoint.  u_out must hold
+ * 2 * 4^k doubles (at most 2 * 1024); *k_out receives k.  Host only. */
+sv_status sv_gate_matrix(uint32_t kind, const double *params, uint32_t nparams, int dagger,
+                         double *u_out, uint32_t *k_out);
+
+/* --------------------------------------------------------------------- states */
+
+/* Create an n-qubit state (1 <= n <= SV_MAX_QUBITS) in dtype on the current CUDA
+ * device, initialised to |0...0>.
+ *   dev_buf: caller-owned device buffer of `bytes` bytes (16-byte aligned, at least
+ *            2^n * 8 (C64) or 2^n * 16 (C128) bytes), or NULL for a library-owned
+ *            buffer of exactly the state's size.  A caller buffer must outlive the state.
+ *   stream:  cudaStream_t to enqueue all work on (NULL = the legacy default stream).
+ * The library also allocates a small workspace (reduction partials, top-k candidates,
+ * the error word).  Returns SV_ERR_OOM if an allocation fails. */
+sv_status sv_alloc(uint32_t n, sv_dtype dtype, void *dev_buf, size_t bytes, void *stream,
+                   sv_state **out);
+sv_status sv_free(sv_state *s);                      /* synchronises, frees owned memory */
+sv_status sv_info(const sv_state *s, uint32_t *n, sv_dtype *dtype, void **dev_ptr);
+
+/* |x> (x < 2^n).  Asynchronous. */
+sv_status sv_set_basis(sv_state *s, uint64_t x);
+/* Copy 2^n amplitudes in the state's dtype from src (host or device memory).  Host
+ * sources are copied synchronously; pinned host memory is fastest. */
+sv_status sv_set_state(sv_state *s, const void *src, int src_on_device);
+/* Copy the 2^n amplitudes (state's dtype, logical qubit order) to dst.  To host:
+ * synchronises.  To device: asynchronous. */
+sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device);
+
+/* ------------------------------------------------------------------ fusion (F) */
+
+/* DAG-based gate fusion, Section 5.1-5.2 (Eq. 8 DAG, Algorithm 2, Eq. 9 product).
+ * Gates fuse along DAG edges while the union of their qubits has at most max_k
+ * members and contracting the edge keeps the DAG acyclic; U_fused = U_v . U_u in FP64.
+ * max_k = 0 returns the gates unfused.  Sweeps repeat in min-id topological order
+ * until nothing changes; the result is deterministic.  Fused targets are sorted
+ * ascending.  Gates wider than max_k are kept as they are (k <= SV_MAX_K).
+ * Copies the matrices; free the result with sv_circuit_free.  Host only. */
+sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k,
+                  sv_circuit **out);
+sv_status sv_circuit_free(sv_circuit *c);
+/* Number of fused gates and the qubit count the circuit was built for. */
+sv_status sv_circuit_size(const sv_circuit *c, size_t *nfused, uint32_t *n);
+/* Gate i of the schedule: k, targets (k entries, ascending) and matrix (2 * 4^k
+ * doubles; may be NULL to skip). */
+sv_status sv_circuit_gate(const sv_circuit *c, size_t i, uint32_t *k, uint32_t *targets,
+                          double *u);
+
+/* ------------------------------------------------------- precision (R) and apply (E) */
+
+/* A-priori rule of Eqs. 11-12: eps_round = g * 2^n * 1.19e-7; complex64 iff
+ * eps_round <= eps_tol.  Host only. */
+sv_status sv_choose_dtype(uint32_t n, uint64_t g, double eps_tol, sv_dtype *out,
+                          double *eps_round);
+
+typedef struct {
+    uint32_t adaptive;          /* 1: runtime c64 -> c128 promotion on norm drift */
+    double drift_threshold;     /* promote when |norm - norm_before| > this (1e-6) */
+    uint32_t drift_check_every; /* check after every S passes (0: only at the end) */
+    uint32_t timing;            /* 1: time the gate passes with CUDA events (synchronises) */
+} sv_apply_opts;
+
+typedef struct {
+    int32_t dtype_used;         /* sv_dtype that produced the final state */
+    uint32_t promotions;        /* 1 if the circuit was replayed in complex128 */
+    uint64_t passes;            /* gate passes enqueued (including a replay) */
+    double norm_before;         /* FP64 norms measured when adaptive (else 0) */
+    double norm_after;
+    double drift;               /* |norm_after - norm_before| of the reported run */
+    uint64_t bytes;             /* algorithmic HBM bytes of the passes: passes * 2 * 2^n * s */
+    double apply_ms;            /* with opts->timing: CUDA-event time of all passes (ms) */
+} sv_apply_report;
+
+/* Apply every gate of the fused schedule, in order, one pass over the state each.
+ * opts may be NULL (no adaptivity).  With opts->adaptive and a C64 state, the FP64 norm
+ * is measured before and after (and every drift_check_every passes); if the drift
+ * exceeds drift_threshold the state is re-initialised in complex128 from its value at
+ * the start of the call and the whole schedule is replayed in complex128 (Section 5.4
+ * made runtime).  Promotion needs a buffer of 2^n * 16 bytes: a library-owned buffer is
+ * reallocated, a caller buffer must already be that large (else SV_ERR_STATE).  report
+ * may be NULL.  Asynchronous unless adaptive. */
+sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts *opts,
+                           sv_apply_report *report);
+
+/* Apply one gate (unfused per-gate form; targets in any order).  Asynchronous. */
+sv_status sv_apply_gate(sv_state *s, const sv_gate *g);
+
+/* ------------------------------------------------------------------ reductions */
+
+/* sum_k |alpha_k|^2 accumulated in FP64 (Eq. 1).  Synchronises. */
+sv_status sv_norm(sv_state *s, double *out);
+/* p_k = |alpha_k|^2 for all 2^n outcomes in index order: float (C64) or double (C128).
+ * out_on_device: out is device memory (asynchronous) or host memory (synchronises). */
+sv_status sv_probs(sv_state *s, void *out, int out_on_device);
+/* out = sum_t coef[t] <psi| P_t |psi> for Pauli strings P_t given by xmask[t] (X or Y
+ * on those qubits) and zmask[t] (Z or Y): P|k> = i^{|x&z|} (-1)^{|k&z|} |k^x>.
+ * Accumulated in FP64.  Synchronises. */
+sv_status sv_expect(sv_state *s, const uint64_t *xmask, const uint64_t *zmask,
+                    const double *coef, size_t nterms, double *out);
+/* The min(k, 2^n) most probable outcomes (1 <= k <= 64), sorted by probability
+ * descending, ties to the lower index.  idx/p are host arrays of k entries.  Synchronises. */
+sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
+
+sv_status sv_sync(sv_state *s);   /* wait for the state's stream; reports device errors */
+const char *sv_last_error(void);  /* thread-local, never NULL */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SV_GB300_H */

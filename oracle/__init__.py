@@ -152,6 +152,24 @@ def fidelity(a: np.ndarray, b: np.ndarray) -> float:
     return abs(inner(a, b)) ** 2
 
 
+def probs_in_precision(psi: np.ndarray) -> np.ndarray:
+    """p_k = |alpha_k|^2 evaluated as fl(fl(re*re) + fl(im*im)) in the precision of psi
+    (float32 for complex64).  Where a floating-point value decides an integer result
+    (the top-k indices), the oracle takes that decision in the kernel's precision."""
+    re, im = psi.real.copy(), psi.imag.copy()
+    return re * re + im * im
+
+
+def topk_valid(idx: np.ndarray, p_exact: np.ndarray, k: int, tol: float) -> bool:
+    """True if idx (distinct indices) is a correct top-k of p_exact up to ties within
+    tol: the j-th listed outcome has probability within tol of the j-th largest."""
+    if len(set(int(i) for i in idx)) != len(idx):
+        return False
+    best = np.sort(p_exact)[::-1][: min(k, p_exact.size)]
+    got = p_exact[np.asarray(idx, dtype=np.int64)]
+    return len(idx) == best.size and bool(np.all(np.abs(got - best) <= tol))
+
+
 def topk(p: np.ndarray, k: int) -> Tuple[np.ndarray, np.ndarray]:
     """The k largest probabilities, ties to the lower index (a stable sort on -p)."""
     order = np.argsort(-p, kind="stable")[:k]

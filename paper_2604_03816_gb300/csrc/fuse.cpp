@@ -1,0 +1,185 @@
+// DAG-based gate fusion: Section 5.1 (DAG construction, Eq. 8) and Section 5.2
+// (Algorithm 2, U_fused = U_v . U_u of Eq. 9).  Host code; matrix products in FP64.
+//
+// DAG: scanning gates in order with a "last gate on each qubit" map, an edge (u, v) is
+// added for every qubit of v whose last gate is u (|E| <= sum_v |q(v)|).
+//
+// Sweeps: until a sweep fuses nothing, take the vertices in topological order (Kahn's
+// algorithm, smallest vertex id first); for each surviving vertex v try its
+// predecessors u in ascending id order and fuse the first u with
+//   |q(u) U q(v)| <= max_k   and   no directed path u -> ... -> v other than (u, v),
+// i.e. the contraction keeps the graph acyclic, which is how Algorithm 2's "u is the
+// sole predecessor of v on the shared qubits" is read here (it also excludes detours
+// through other qubits).  u absorbs v: U_u <- E(U_v) . E(U_u) on the sorted union of
+// their qubits (E = embedding with identities), v's in- and out-edges move to u, and u
+// keeps its id.  The final schedule lists the survivors in the same topological order.
+#include <algorithm>
+#include <queue>
+#include <set>
+
+#include "sv_internal.h"
+
+namespace svi {
+namespace {
+
+struct Node {
+    bool alive = true;
+    Gate g;
+    std::set<int> preds, succs;   // ordered: predecessors are tried in ascending id
+};
+
+// Matrix of gate g (sorted targets) embedded on the sorted qubit set qs (size m).
+std::vector<cplx> embed(const Gate &g, const uint32_t *qs, uint32_t m) {
+    int pos[SV_MAX_K];
+    uint32_t amask = 0;
+    for (uint32_t j = 0; j < g.k; ++j) {
+        uint32_t p = 0;
+        while (qs[p] != g.t[j]) ++p;
+        pos[j] = (int)p;
+        amask |= 1u << p;
+    }
+    const int d = 1 << m, dg = 1 << g.k;
+    std::vector<cplx> e((size_t)d * d, cplx(0.0, 0.0));
+    for (int r = 0; r < d; ++r) {
+        int er = 0;
+        for (uint32_t j = 0; j < g.k; ++j) er |= ((r >> pos[j]) & 1) << j;
+        for (int c = 0; c < d; ++c) {
+            if ((r & ~amask) != (c & ~amask)) continue;
+            int ec = 0;
+            for (uint32_t j = 0; j < g.k; ++j) ec |= ((c >> pos[j]) & 1) << j;
+            e[(size_t)r * d + c] = g.u[(size_t)er * dg + ec];
+        }
+    }
+    return e;
+}
+
+class Dag {
+  public:
+    Dag(const std::vector<Gate> &gates, uint32_t n) : nodes_(gates.size()), seen_(gates.size(), 0) {
+        std::vector<int> last(n, -1);
+        for (size_t i = 0; i < gates.size(); ++i) {
+            nodes_[i].g = gates[i];
+            for (uint32_t j = 0; j < gates[i].k; ++j) {
+                const uint32_t q = gates[i].t[j];
+                if (last[q] >= 0) {
+                    nodes_[i].preds.insert(last[q]);
+                    nodes_[last[q]].succs.insert((int)i);
+                }
+                last[q] = (int)i;
+            }
+        }
+    }
+
+    std::vector<int> topo_order() const {
+        std::vector<int> indeg(nodes_.size(), 0);
+        std::priority_queue<int, std::vector<int>, std::greater<int>> ready;
+        for (size_t v = 0; v < nodes_.size(); ++v) {
+            if (!nodes_[v].alive) continue;
+            indeg[v] = (int)nodes_[v].preds.size();
+            if (indeg[v] == 0) ready.push((int)v);
+        }
+        std::vector<int> out;
+        while (!ready.empty()) {
+            const int v = ready.top();
+            ready.pop();
+            out.push_back(v);
+            for (int w : nodes_[v].succs)
+                if (--indeg[w] == 0) ready.push(w);
+        }
+        return out;
+    }
+
+    bool other_path(int u, int v) {
+        ++stamp_;
+        std::vector<int> stack;
+        for (int w : nodes_[u].succs)
+            if (w != v) { stack.push_back(w); seen_[w] = stamp_; }
+        while (!stack.empty()) {
+            const int w = stack.back();
+            stack.pop_back();
+            if (w == v) return true;
+            for (int x : nodes_[w].succs)
+                if (seen_[x] != stamp_) { seen_[x] = stamp_; stack.push_back(x); }
+        }
+        return false;
+    }
+
+    static uint32_t union_qubits(const Gate &a, const Gate &b, uint32_t *qs) {
+        uint32_t m = 0;
+        uint32_t i = 0, j = 0;
+        while (i < a.k || j < b.k) {
+            uint32_t x;
+            if (j >= b.k || (i < a.k && a.t[i] < b.t[j])) x = a.t[i++];
+            else if (i >= a.k || b.t[j] < a.t[i]) x = b.t[j++];
+            else { x = a.t[i]; ++i; ++j; }
+            if (m < 2 * SV_MAX_K) qs[m] = x;
+            ++m;
+        }
+        return m;
+    }
+
+    void contract(int u, int v, const uint32_t *qs, uint32_t m) {
+        Node &U = nodes_[u], &V = nodes_[v];
+        const std::vector<cplx> eu = embed(U.g, qs, m), ev = embed(V.g, qs, m);
+        const int d = 1 << m;
+        Gate f;
+        f.k = m;
+        for (uint32_t j = 0; j < m; ++j) f.t[j] = qs[j];
+        f.u.assign((size_t)d * d, cplx(0.0, 0.0));
+        for (int r = 0; r < d; ++r)            // Eq. 9: U_fused = U_v . U_u
+            for (int x = 0; x < d; ++x) {
+                const cplx a = ev[(size_t)r * d + x];
+                if (a == cplx(0.0, 0.0)) continue;
+                for (int c = 0; c < d; ++c) f.u[(size_t)r * d + c] += a * eu[(size_t)x * d + c];
+            }
+        U.g = std::move(f);
+        for (int w : V.preds)
+            if (w != u) {
+                nodes_[w].succs.erase(v);
+                nodes_[w].succs.insert(u);
+                U.preds.insert(w);
+            }
+        for (int w : V.succs) {
+            nodes_[w].preds.erase(v);
+            nodes_[w].preds.insert(u);
+            U.succs.insert(w);
+        }
+        U.succs.erase(v);
+        V.alive = false;
+        V.preds.clear();
+        V.succs.clear();
+        V.g.u.clear();
+    }
+
+    std::vector<Node> nodes_;
+    std::vector<uint32_t> seen_;
+    uint32_t stamp_ = 0;
+};
+
+}  // namespace
+
+std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k) {
+    Dag dag(in, n);
+    bool changed = max_k > 0;
+    while (changed) {
+        changed = false;
+        for (int v : dag.topo_order()) {
+            if (!dag.nodes_[v].alive) continue;
+            const std::vector<int> preds(dag.nodes_[v].preds.begin(), dag.nodes_[v].preds.end());
+            for (int u : preds) {
+                uint32_t qs[2 * SV_MAX_K];
+                const uint32_t m = Dag::union_qubits(dag.nodes_[u].g, dag.nodes_[v].g, qs);
+                if (m > max_k) continue;
+                if (dag.other_path(u, v)) continue;
+                dag.contract(u, v, qs, m);
+                changed = true;
+                break;
+            }
+        }
+    }
+    std::vector<Gate> out;
+    for (int v : dag.topo_order()) out.push_back(dag.nodes_[v].g);
+    return out;
+}
+
+}  // namespace svi

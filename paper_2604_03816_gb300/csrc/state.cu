@@ -1,0 +1,420 @@
+// C-ABI implementation: states, fusion entry points, the precision controller and the
+// apply / reduction calls.  Argument checking happens here; the kernels live in
+// apply_kernels.cu and reduce_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sv_internal.h"
+
+namespace svi {
+
+static thread_local std::string g_err;
+
+sv_status set_error(sv_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+void clear_error() { g_err.clear(); }
+
+static size_t elem_bytes(sv_dtype d) { return d == SV_C64 ? 8 : 16; }
+static size_t state_bytes(const sv_state *s) { return elem_bytes(s->dtype) << s->n; }
+
+sv_status check_device_error(sv_state *s) {
+    SV_CUDA(cudaStreamSynchronize(s->stream));
+    int err = 0;
+    SV_CUDA(cudaMemcpy(&err, s->ws + WS_ERR, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) {
+        SV_CUDA(cudaMemset(s->ws + WS_ERR, 0, sizeof(int)));
+        return set_error(SV_ERR_TIMEOUT, "a bounded device-side wait gave up (error word " +
+                                             std::to_string(err) + ")");
+    }
+    return SV_OK;
+}
+
+static sv_status validate_gate(const sv_gate *g, uint32_t n, const char *who) {
+    if (!g || !g->u) return set_error(SV_ERR_ARG, std::string(who) + ": null gate or matrix");
+    if (g->k < 1 || g->k > SV_MAX_K)
+        return set_error(SV_ERR_ARG, std::string(who) + ": gate width must be 1..5");
+    uint64_t seen = 0;
+    for (uint32_t j = 0; j < g->k; ++j) {
+        if (g->targets[j] >= n)
+            return set_error(SV_ERR_ARG, std::string(who) + ": target " +
+                                             std::to_string(g->targets[j]) + " >= n");
+        if (seen & (1ull << g->targets[j]))
+            return set_error(SV_ERR_ARG, std::string(who) + ": repeated target");
+        seen |= 1ull << g->targets[j];
+    }
+    return SV_OK;
+}
+
+static sv_status measure_norm(sv_state *s, double *out) {
+    double *res = reinterpret_cast<double *>(s->ws + WS_RESULT) + 63;
+    sv_status st = launch_norm(s, res);
+    if (st != SV_OK) return st;
+    SV_CUDA(cudaMemcpyAsync(out, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    return check_device_error(s);
+}
+
+}  // namespace svi
+
+using namespace svi;
+
+extern "C" {
+
+const char *sv_last_error(void) { return g_err.c_str(); }
+
+sv_status sv_alloc(uint32_t n, sv_dtype dtype, void *dev_buf, size_t bytes, void *stream,
+                   sv_state **out) {
+    clear_error();
+    if (!out) return set_error(SV_ERR_ARG, "sv_alloc: null out");
+    *out = nullptr;
+    if (n < 1 || n > SV_MAX_QUBITS) return set_error(SV_ERR_ARG, "sv_alloc: n must be 1..34");
+    if (dtype != SV_C64 && dtype != SV_C128) return set_error(SV_ERR_ARG, "sv_alloc: bad dtype");
+    const size_t need = elem_bytes(dtype) << n;
+    if (dev_buf) {
+        if (bytes < need) return set_error(SV_ERR_ARG, "sv_alloc: buffer smaller than 2^n amplitudes");
+        if (reinterpret_cast<uintptr_t>(dev_buf) & 15u)
+            return set_error(SV_ERR_ARG, "sv_alloc: buffer must be 16-byte aligned");
+    }
+    sv_state *s = new (std::nothrow) sv_state();
+    if (!s) return set_error(SV_ERR_OOM, "sv_alloc: host allocation failed");
+    s->n = n;
+    s->dtype = dtype;
+    s->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) {
+        delete s;
+        return set_error(SV_ERR_CUDA, std::string("sv_alloc: ") + cudaGetErrorString(e));
+    }
+    if (dev_buf) {
+        s->buf = dev_buf;
+        s->cap = bytes;
+        s->owned = false;
+    } else {
+        e = cudaMalloc(&s->buf, need);
+        if (e != cudaSuccess) {
+            delete s;
+            return set_error(SV_ERR_OOM, std::string("sv_alloc: state: ") + cudaGetErrorString(e));
+        }
+        s->cap = need;
+        s->owned = true;
+    }
+    e = cudaMalloc(reinterpret_cast<void **>(&s->ws), WS_BYTES);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ws, 0, WS_BYTES, s->stream);
+    if (e != cudaSuccess) {
+        if (s->owned) cudaFree(s->buf);
+        if (s->ws) cudaFree(s->ws);
+        delete s;
+        return set_error(SV_ERR_OOM, std::string("sv_alloc: workspace: ") + cudaGetErrorString(e));
+    }
+    sv_status st = sv_set_basis(s, 0);
+    if (st != SV_OK) {
+        sv_free(s);
+        return st;
+    }
+    *out = s;
+    return SV_OK;
+}
+
+sv_status sv_free(sv_state *s) {
+    clear_error();
+    if (!s) return SV_OK;
+    cudaStreamSynchronize(s->stream);
+    if (s->owned && s->buf) cudaFree(s->buf);
+    if (s->ws) cudaFree(s->ws);
+    if (s->snap) cudaFree(s->snap);
+    delete s;
+    return SV_OK;
+}
+
+sv_status sv_info(const sv_state *s, uint32_t *n, sv_dtype *dtype, void **dev_ptr) {
+    clear_error();
+    if (!s) return set_error(SV_ERR_ARG, "sv_info: null state");
+    if (n) *n = s->n;
+    if (dtype) *dtype = s->dtype;
+    if (dev_ptr) *dev_ptr = s->buf;
+    return SV_OK;
+}
+
+sv_status sv_set_basis(sv_state *s, uint64_t x) {
+    clear_error();
+    if (!s) return set_error(SV_ERR_ARG, "sv_set_basis: null state");
+    if (x >> s->n) return set_error(SV_ERR_ARG, "sv_set_basis: x >= 2^n");
+    SV_CUDA(cudaMemsetAsync(s->buf, 0, state_bytes(s), s->stream));
+    sv_status st = launch_set_one(s, x);
+    if (st != SV_OK) return st;
+    s->basis_known = true;
+    s->basis_x = x;
+    return SV_OK;
+}
+
+sv_status sv_set_state(sv_state *s, const void *src, int src_on_device) {
+    clear_error();
+    if (!s || !src) return set_error(SV_ERR_ARG, "sv_set_state: null argument");
+    SV_CUDA(cudaMemcpyAsync(s->buf, src, state_bytes(s),
+                            src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s->stream));
+    s->basis_known = false;
+    if (!src_on_device) SV_CUDA(cudaStreamSynchronize(s->stream));
+    return SV_OK;
+}
+
+sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device) {
+    clear_error();
+    if (!s || !dst) return set_error(SV_ERR_ARG, "sv_get_state: null argument");
+    SV_CUDA(cudaMemcpyAsync(dst, s->buf, state_bytes(s),
+                            dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            s->stream));
+    if (!dst_on_device) return check_device_error(s);
+    return SV_OK;
+}
+
+sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k,
+                  sv_circuit **out) {
+    clear_error();
+    if (!out) return set_error(SV_ERR_ARG, "sv_fuse: null out");
+    *out = nullptr;
+    if (n < 1 || n > SV_MAX_QUBITS) return set_error(SV_ERR_ARG, "sv_fuse: n must be 1..34");
+    if (max_k > SV_MAX_K) return set_error(SV_ERR_ARG, "sv_fuse: max_k must be 0..5");
+    if (ngates && !gates) return set_error(SV_ERR_ARG, "sv_fuse: null gates");
+    std::vector<Gate> in;
+    in.reserve(ngates);
+    for (size_t i = 0; i < ngates; ++i) {
+        sv_status st = validate_gate(&gates[i], n, "sv_fuse");
+        if (st != SV_OK) return set_error(st, sv_last_error() + (" (gate " + std::to_string(i) + ")"));
+        in.push_back(sorted_gate(gates[i].k, gates[i].targets, gates[i].u));
+    }
+    sv_circuit *c = new (std::nothrow) sv_circuit();
+    if (!c) return set_error(SV_ERR_OOM, "sv_fuse: host allocation failed");
+    c->n = n;
+    try {
+        c->gates = fuse_gates(in, n, max_k);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return set_error(SV_ERR_OOM, "sv_fuse: host allocation failed");
+    }
+    *out = c;
+    return SV_OK;
+}
+
+sv_status sv_circuit_free(sv_circuit *c) {
+    delete c;
+    return SV_OK;
+}
+
+sv_status sv_circuit_size(const sv_circuit *c, size_t *nfused, uint32_t *n) {
+    clear_error();
+    if (!c) return set_error(SV_ERR_ARG, "sv_circuit_size: null circuit");
+    if (nfused) *nfused = c->gates.size();
+    if (n) *n = c->n;
+    return SV_OK;
+}
+
+sv_status sv_circuit_gate(const sv_circuit *c, size_t i, uint32_t *k, uint32_t *targets, double *u) {
+    clear_error();
+    if (!c || i >= c->gates.size()) return set_error(SV_ERR_ARG, "sv_circuit_gate: bad index");
+    const Gate &g = c->gates[i];
+    if (k) *k = g.k;
+    if (targets)
+        for (uint32_t j = 0; j < g.k; ++j) targets[j] = g.t[j];
+    if (u)
+        for (size_t j = 0; j < g.u.size(); ++j) {
+            u[2 * j] = g.u[j].real();
+            u[2 * j + 1] = g.u[j].imag();
+        }
+    return SV_OK;
+}
+
+sv_status sv_choose_dtype(uint32_t n, uint64_t g, double eps_tol, sv_dtype *out, double *eps_round) {
+    clear_error();
+    if (!out) return set_error(SV_ERR_ARG, "sv_choose_dtype: null out");
+    const double e = (double)g * std::ldexp(1.0, (int)n) * 1.19e-7;   // Eq. 12
+    *out = e <= eps_tol ? SV_C64 : SV_C128;
+    if (eps_round) *eps_round = e;
+    return SV_OK;
+}
+
+sv_status sv_apply_gate(sv_state *s, const sv_gate *g) {
+    clear_error();
+    if (!s) return set_error(SV_ERR_ARG, "sv_apply_gate: null state");
+    sv_status st = validate_gate(g, s->n, "sv_apply_gate");
+    if (st != SV_OK) return st;
+    s->basis_known = false;
+    return launch_apply(s, sorted_gate(g->k, g->targets, g->u));
+}
+
+// Enqueue passes [begin, end).  With `timing`, CUDA events on the state's stream bracket
+// the passes and their elapsed time is added to *ms (this synchronises on the events).
+static sv_status run_schedule(sv_state *s, const sv_circuit *c, size_t begin, size_t end,
+                              bool timing, sv_apply_report *r) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timing) {
+        SV_CUDA(cudaEventCreate(&e0));
+        SV_CUDA(cudaEventCreate(&e1));
+        SV_CUDA(cudaEventRecord(e0, s->stream));
+    }
+    sv_status st = SV_OK;
+    for (size_t i = begin; i < end && st == SV_OK; ++i) st = launch_apply(s, c->gates[i]);
+    r->passes += end - begin;
+    r->bytes += (uint64_t)(end - begin) * 2ull * ((uint64_t)elem_bytes(s->dtype) << s->n);
+    if (timing) {
+        cudaError_t e = cudaEventRecord(e1, s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (e != cudaSuccess && st == SV_OK)
+            st = set_error(SV_ERR_CUDA, std::string("apply timing: ") + cudaGetErrorString(e));
+        r->apply_ms += ms;
+    }
+    return st;
+}
+
+sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts *opts,
+                           sv_apply_report *rep) {
+    clear_error();
+    if (!s || !c) return set_error(SV_ERR_ARG, "sv_apply_circuit: null argument");
+    if (c->n != s->n) return set_error(SV_ERR_ARG, "sv_apply_circuit: circuit built for another n");
+    for (const Gate &g : c->gates)
+        if (g.k > s->n) return set_error(SV_ERR_ARG, "sv_apply_circuit: gate wider than the state");
+    sv_apply_report r;
+    std::memset(&r, 0, sizeof(r));
+    r.dtype_used = s->dtype;
+    const size_t G = c->gates.size();
+    const bool adaptive = opts && opts->adaptive && s->dtype == SV_C64;
+    const bool timing = opts && opts->timing;
+    if (!adaptive) {
+        s->basis_known = false;
+        sv_status st = run_schedule(s, c, 0, G, timing, &r);
+        if (st != SV_OK) return st;
+        if (rep) *rep = r;
+        return SV_OK;
+    }
+    const double thr = opts->drift_threshold > 0 ? opts->drift_threshold : 1e-6;
+    const size_t every = opts->drift_check_every;
+    // Remember the initial state for a replay: a basis index or a snapshot.
+    const bool from_basis = s->basis_known;
+    const uint64_t x0 = s->basis_x;
+    const size_t bytes64 = size_t(8) << s->n;
+    if (!from_basis) {
+        if (s->snap_cap < bytes64) {
+            if (s->snap) cudaFree(s->snap);
+            s->snap = nullptr;
+            s->snap_cap = 0;
+            SV_CUDA(cudaMalloc(&s->snap, bytes64));
+            s->snap_cap = bytes64;
+        }
+        SV_CUDA(cudaMemcpyAsync(s->snap, s->buf, bytes64, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    sv_status st = measure_norm(s, &r.norm_before);
+    if (st != SV_OK) return st;
+    s->basis_known = false;
+    bool promote = false;
+    size_t done = 0;
+    while (done < G && !promote) {
+        const size_t next = every ? std::min(G, done + every) : G;
+        st = run_schedule(s, c, done, next, timing, &r);
+        if (st != SV_OK) return st;
+        done = next;
+        st = measure_norm(s, &r.norm_after);
+        if (st != SV_OK) return st;
+        r.drift = std::fabs(r.norm_after - r.norm_before);
+        promote = r.drift > thr;
+    }
+    if (promote) {
+        // Replay the whole schedule in complex128 from the initial state.
+        const size_t bytes128 = size_t(16) << s->n;
+        if (s->cap < bytes128) {
+            if (!s->owned)
+                return set_error(SV_ERR_STATE, "sv_apply_circuit: promotion to complex128 needs a "
+                                               "caller buffer of 2^n * 16 bytes");
+            SV_CUDA(cudaStreamSynchronize(s->stream));
+            SV_CUDA(cudaFree(s->buf));
+            s->buf = nullptr;
+            s->cap = 0;
+            SV_CUDA(cudaMalloc(&s->buf, bytes128));
+            s->cap = bytes128;
+        }
+        s->dtype = SV_C128;
+        if (from_basis) {
+            st = sv_set_basis(s, x0);
+        } else {
+            st = launch_widen(s, s->snap, s->buf);
+        }
+        if (st != SV_OK) return st;
+        s->basis_known = false;
+        st = run_schedule(s, c, 0, G, timing, &r);
+        if (st != SV_OK) return st;
+        r.promotions = 1;
+        r.dtype_used = SV_C128;
+        st = measure_norm(s, &r.norm_after);
+        if (st != SV_OK) return st;
+        r.drift = std::fabs(r.norm_after - r.norm_before);
+    }
+    if (rep) *rep = r;
+    return SV_OK;
+}
+
+sv_status sv_norm(sv_state *s, double *out) {
+    clear_error();
+    if (!s || !out) return set_error(SV_ERR_ARG, "sv_norm: null argument");
+    return measure_norm(s, out);
+}
+
+sv_status sv_probs(sv_state *s, void *out, int out_on_device) {
+    clear_error();
+    if (!s || !out) return set_error(SV_ERR_ARG, "sv_probs: null argument");
+    if (out_on_device) return launch_probs(s, out);
+    const size_t bytes = (s->dtype == SV_C64 ? 4 : 8) << s->n;
+    void *tmp = nullptr;
+    SV_CUDA(cudaMallocAsync(&tmp, bytes, s->stream));
+    sv_status st = launch_probs(s, tmp);
+    if (st == SV_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
+        if (e != cudaSuccess) st = set_error(SV_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaFreeAsync(tmp, s->stream);
+    if (st != SV_OK) return st;
+    return check_device_error(s);
+}
+
+sv_status sv_expect(sv_state *s, const uint64_t *xmask, const uint64_t *zmask, const double *coef,
+                    size_t nterms, double *out) {
+    clear_error();
+    if (!s || !out || (nterms && (!xmask || !zmask || !coef)))
+        return set_error(SV_ERR_ARG, "sv_expect: null argument");
+    const uint64_t lim = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
+    for (size_t t = 0; t < nterms; ++t)
+        if ((xmask[t] & ~lim) || (zmask[t] & ~lim))
+            return set_error(SV_ERR_ARG, "sv_expect: Pauli mask names a qubit >= n");
+    if (nterms == 0) {
+        *out = 0.0;
+        return SV_OK;
+    }
+    sv_status st = launch_expect(s, xmask, zmask, coef, nterms, out);
+    if (st != SV_OK) return st;
+    return check_device_error(s);
+}
+
+sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
+    clear_error();
+    if (!s || !idx || !p) return set_error(SV_ERR_ARG, "sv_topk: null argument");
+    if (k < 1 || k > 64) return set_error(SV_ERR_ARG, "sv_topk: k must be 1..64");
+    sv_status st = launch_topk(s, k, idx, p);
+    if (st != SV_OK) return st;
+    return check_device_error(s);
+}
+
+sv_status sv_sync(sv_state *s) {
+    clear_error();
+    if (!s) return set_error(SV_ERR_ARG, "sv_sync: null state");
+    return check_device_error(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sv.h"
+
+namespace svi {
+
+using cplx = std::complex<double>;
+
+// Thread-local last error message; set() returns the status for `return svi::set(...)`.
+sv_status set_error(sv_status st, const std::string &msg);
+void clear_error();
+
+// A gate on sorted targets with its FP64 matrix (row-major, 2^k x 2^k).
+struct Gate {
+    uint32_t k = 0;
+    uint32_t t[SV_MAX_K] = {0, 0, 0, 0, 0};
+    std::vector<cplx> u;
+};
+
+// Relabel a gate's local bits so that its targets are ascending (same operator).
+Gate sorted_gate(uint32_t k, const uint32_t *targets, const double *u);
+
+// Algorithm 2 over sorted gates (fuse.cpp).
+std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k);
+
+}  // namespace svi
+
+struct sv_circuit {
+    uint32_t n = 0;
+    std::vector<svi::Gate> gates;
+};
+
+// Device workspace layout (bytes), carved from one allocation.
+namespace svi {
+constexpr size_t WS_ERR = 0;                   // int error word (+ padding)
+constexpr size_t WS_PARTIAL = 256;             // double partials[WS_NPARTIAL]
+constexpr int WS_NPARTIAL = 8192;
+constexpr size_t WS_RESULT = WS_PARTIAL + WS_NPARTIAL * 8;   // double results[64]
+constexpr size_t WS_TOPK = WS_RESULT + 64 * 8;               // top-k candidates
+constexpr int TOPK_MAX_WARPS = 4096;
+constexpr size_t WS_TOPK_BYTES = size_t(TOPK_MAX_WARPS) * 64 * 16;
+constexpr size_t WS_BYTES = WS_TOPK + WS_TOPK_BYTES + 64 * 16;
+}  // namespace svi
+
+struct sv_state {
+    uint32_t n = 0;
+    sv_dtype dtype = SV_C64;
+    void *buf = nullptr;        // amplitudes
+    size_t cap = 0;             // bytes available at buf
+    bool owned = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    unsigned char *ws = nullptr;   // device workspace (WS_BYTES)
+    // what the state holds, for adaptive replay: a basis state or a snapshot
+    bool basis_known = true;
+    uint64_t basis_x = 0;
+    void *snap = nullptr;       // library-owned snapshot of the initial state (c64)
+    size_t snap_cap = 0;
+    int num_sms = 0;
+};
+
+namespace svi {
+// ---- kernels (apply_kernels.cu / reduce_kernels.cu); all enqueue on s->stream ----
+sv_status launch_apply(sv_state *s, const Gate &g);
+sv_status launch_norm(sv_state *s, double *dev_out);     // writes one double on device
+sv_status launch_probs(sv_state *s, void *dev_out);
+sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const double *c,
+                        size_t nterms, double *host_out);
+sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
+sv_status launch_widen(sv_state *s, const void *src_c64, void *dst_c128);
+sv_status launch_set_one(sv_state *s, uint64_t x);
+sv_status check_device_error(sv_state *s);   // synchronises; reads and clears the error word
+}  // namespace svi
+
+#define SV_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return svi::set_error(e_ == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA, \
+                                  std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)

@@ -1,0 +1,329 @@
+"""Thin Python binding of the C ABI in include/sv.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device memory and streams
+may come from PyTorch (a CUDA tensor's data_ptr and torch.cuda.current_stream()); all
+computation happens in libsvgb300.so.  Importing this module fails loudly when the
+library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsvgb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(LIB_PATH)
+
+SV_C64, SV_C128 = 0, 1
+SV_MAX_K = 5
+STATUS = {0: "SV_OK", 1: "SV_ERR_ARG", 2: "SV_ERR_OOM", 3: "SV_ERR_CUDA", 4: "SV_ERR_TIMEOUT",
+          5: "SV_ERR_STATE"}
+GATE_KINDS = {"i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "t": 6, "rx": 7, "ry": 8, "rz": 9,
+              "cnot": 10, "cz": 11, "swap": 12, "toffoli": 13, "u3": 14, "sqrtx": 15,
+              "sqrty": 16, "sqrtw": 17, "fsim": 18, "cp": 19, "unitary": 20}
+
+EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "sv_set_state",
+           "sv_get_state", "sv_fuse", "sv_circuit_free", "sv_circuit_size", "sv_circuit_gate",
+           "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
+           "sv_expect", "sv_topk", "sv_sync", "sv_last_error"]
+
+
+class SvError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sv_gate(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("targets", ctypes.c_uint32 * SV_MAX_K),
+                ("u", ctypes.POINTER(ctypes.c_double))]
+
+
+class sv_apply_opts(ctypes.Structure):
+    _fields_ = [("adaptive", ctypes.c_uint32), ("drift_threshold", ctypes.c_double),
+                ("drift_check_every", ctypes.c_uint32), ("timing", ctypes.c_uint32)]
+
+
+class sv_apply_report(ctypes.Structure):
+    _fields_ = [("dtype_used", ctypes.c_int32), ("promotions", ctypes.c_uint32),
+                ("passes", ctypes.c_uint64), ("norm_before", ctypes.c_double),
+                ("norm_after", ctypes.c_double), ("drift", ctypes.c_double),
+                ("bytes", ctypes.c_uint64), ("apply_ms", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_dp = ctypes.POINTER(ctypes.c_double)
+_sig = {
+    "sv_gate_matrix": [_u32, _dp, _u32, _i32, _dp, ctypes.POINTER(_u32)],
+    "sv_alloc": [_u32, _i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
+    "sv_free": [_vp],
+    "sv_info": [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_vp)],
+    "sv_set_basis": [_vp, _u64],
+    "sv_set_state": [_vp, _vp, _i32],
+    "sv_get_state": [_vp, _vp, _i32],
+    "sv_fuse": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32, ctypes.POINTER(_vp)],
+    "sv_circuit_free": [_vp],
+    "sv_circuit_size": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_u32)],
+    "sv_circuit_gate": [_vp, ctypes.c_size_t, ctypes.POINTER(_u32), ctypes.POINTER(_u32), _dp],
+    "sv_choose_dtype": [_u32, _u64, ctypes.c_double, ctypes.POINTER(_i32), _dp],
+    "sv_apply_circuit": [_vp, _vp, ctypes.POINTER(sv_apply_opts), ctypes.POINTER(sv_apply_report)],
+    "sv_apply_gate": [_vp, ctypes.POINTER(sv_gate)],
+    "sv_norm": [_vp, _dp],
+    "sv_probs": [_vp, _vp, _i32],
+    "sv_expect": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp, ctypes.c_size_t, _dp],
+    "sv_topk": [_vp, _u32, ctypes.POINTER(_u64), _dp],
+    "sv_sync": [_vp],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+_lib.sv_last_error.restype = ctypes.c_char_p
+_lib.sv_last_error.argtypes = []
+
+
+def sv_last_error() -> str:
+    return _lib.sv_last_error().decode()
+
+
+def _check(st: int) -> None:
+    if st != 0:
+        raise SvError(st, sv_last_error())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+# --------------------------------------------------------------------------- gates
+
+def sv_gate_matrix(name: str, params: Sequence[float] = (), dagger: bool = False,
+                   matrix=None) -> np.ndarray:
+    """Matrix (complex128, 2^k x 2^k) of a gate of the canonical set, built by the library."""
+    kind = GATE_KINDS[name]
+    if name == "unitary":
+        m = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128).ravel())
+        p = m.view(np.float64)
+    else:
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float64))
+    out = np.zeros(2 * 1024, dtype=np.float64)
+    k = _u32()
+    _check(_lib.sv_gate_matrix(kind, _ptr(p) if p.size else None, p.size, int(bool(dagger)),
+                               _ptr(out), ctypes.byref(k)))
+    d = 1 << k.value
+    return out[: 2 * d * d].view(np.complex128).reshape(d, d).copy()
+
+
+class GateArray:
+    """A ctypes array of sv_gate plus the matrices it points to (kept alive)."""
+
+    def __init__(self, gates: Sequence[Tuple[Sequence[int], np.ndarray]]):
+        self.mats = [np.ascontiguousarray(np.asarray(u, dtype=np.complex128)) for _, u in gates]
+        self.arr = (sv_gate * max(1, len(gates)))()
+        for i, ((tg, _), m) in enumerate(zip(gates, self.mats)):
+            self.arr[i].k = len(tg)
+            for j, t in enumerate(tg[:SV_MAX_K]):     # k > 5 is rejected by the library
+                self.arr[i].targets[j] = int(t)
+            self.arr[i].u = m.view(np.float64).ctypes.data_as(_dp)
+        self.n = len(gates)
+
+
+def gates_from_specs(specs) -> List[Tuple[Tuple[int, ...], np.ndarray]]:
+    """[(targets, U)] for workloads.GateSpec records, matrices from the library."""
+    return [(tuple(g.qubits), sv_gate_matrix(g.name, g.params, g.dagger, g.matrix)) for g in specs]
+
+
+# --------------------------------------------------------------------------- circuits
+
+class Circuit:
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.sv_circuit_free(self.handle)
+            self.handle = None
+
+    def __len__(self) -> int:
+        return sv_circuit_size(self)[0]
+
+
+def sv_fuse(gates: Sequence[Tuple[Sequence[int], np.ndarray]], n: int, max_k: int) -> Circuit:
+    ga = GateArray(gates)
+    h = _vp()
+    _check(_lib.sv_fuse(ga.arr, ga.n, n, max_k, ctypes.byref(h)))
+    return Circuit(h.value)
+
+
+def sv_circuit_size(c: Circuit) -> Tuple[int, int]:
+    nf, n = ctypes.c_size_t(), _u32()
+    _check(_lib.sv_circuit_size(c.handle, ctypes.byref(nf), ctypes.byref(n)))
+    return nf.value, n.value
+
+
+def sv_circuit_gate(c: Circuit, i: int) -> Tuple[Tuple[int, ...], np.ndarray]:
+    k = _u32()
+    tg = (_u32 * SV_MAX_K)()
+    _check(_lib.sv_circuit_gate(c.handle, i, ctypes.byref(k), tg, None))
+    d = 1 << k.value
+    u = np.zeros(2 * d * d, dtype=np.float64)
+    _check(_lib.sv_circuit_gate(c.handle, i, ctypes.byref(k), tg, _ptr(u)))
+    return tuple(int(tg[j]) for j in range(k.value)), u.view(np.complex128).reshape(d, d)
+
+
+def sv_choose_dtype(n: int, g: int, eps_tol: float) -> Tuple[int, float]:
+    out, e = _i32(), ctypes.c_double()
+    _check(_lib.sv_choose_dtype(n, g, eps_tol, ctypes.byref(out), ctypes.byref(e)))
+    return out.value, e.value
+
+
+# --------------------------------------------------------------------------- states
+
+class State:
+    """An sv_state handle.  `keep` holds the caller buffer (e.g. a torch tensor) alive."""
+
+    def __init__(self, handle: int, keep=None):
+        self.handle = handle
+        self.keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.sv_free(self.handle)
+            self.handle = None
+
+    def free(self):
+        if self.handle:
+            _check(_lib.sv_free(self.handle))
+            self.handle = None
+
+    @property
+    def info(self):
+        return sv_info(self)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+def sv_alloc(n: int, dtype: int = SV_C64, dev_buf=None, nbytes: int = 0, stream=None) -> State:
+    """dev_buf: None (library-owned), a CUDA torch tensor, or a raw device pointer."""
+    keep, ptr = None, None
+    if dev_buf is not None:
+        if hasattr(dev_buf, "data_ptr"):
+            keep, ptr = dev_buf, int(dev_buf.data_ptr())
+            nbytes = nbytes or int(dev_buf.numel() * dev_buf.element_size())
+        else:
+            ptr = int(dev_buf)
+    h = _vp()
+    _check(_lib.sv_alloc(n, dtype, ptr, nbytes, _stream_ptr(stream), ctypes.byref(h)))
+    return State(h.value, keep)
+
+
+def sv_free(s: State) -> None:
+    s.free()
+
+
+def sv_info(s: State) -> Tuple[int, int, int]:
+    n, dt, p = _u32(), _i32(), _vp()
+    _check(_lib.sv_info(s.handle, ctypes.byref(n), ctypes.byref(dt), ctypes.byref(p)))
+    return n.value, dt.value, p.value
+
+
+def sv_set_basis(s: State, x: int) -> None:
+    _check(_lib.sv_set_basis(s.handle, x))
+
+
+def _np_dtype(dt: int):
+    return np.complex64 if dt == SV_C64 else np.complex128
+
+
+def sv_set_state(s: State, src) -> None:
+    """src: numpy array (host) or CUDA torch tensor (device), in the state's dtype."""
+    if hasattr(src, "data_ptr"):
+        _check(_lib.sv_set_state(s.handle, int(src.data_ptr()), 1))
+        return
+    n, dt, _ = sv_info(s)
+    a = np.ascontiguousarray(src, dtype=_np_dtype(dt))
+    assert a.size == 1 << n
+    _check(_lib.sv_set_state(s.handle, a.ctypes.data, 0))
+
+
+def sv_get_state(s: State, out=None):
+    """Host numpy copy (default) or into a CUDA torch tensor `out` (asynchronous)."""
+    if out is not None and hasattr(out, "data_ptr"):
+        _check(_lib.sv_get_state(s.handle, int(out.data_ptr()), 1))
+        return out
+    n, dt, _ = sv_info(s)
+    a = out if out is not None else np.empty(1 << n, dtype=_np_dtype(dt))
+    _check(_lib.sv_get_state(s.handle, a.ctypes.data, 0))
+    return a
+
+
+def sv_apply_circuit(s: State, c: Circuit, adaptive: bool = False, drift_threshold: float = 1e-6,
+                     drift_check_every: int = 0, timing: bool = False) -> dict:
+    opts = sv_apply_opts(int(bool(adaptive)), drift_threshold, drift_check_every,
+                         int(bool(timing)))
+    rep = sv_apply_report()
+    _check(_lib.sv_apply_circuit(s.handle, c.handle, ctypes.byref(opts), ctypes.byref(rep)))
+    return {"dtype_used": rep.dtype_used, "promotions": rep.promotions, "passes": rep.passes,
+            "norm_before": rep.norm_before, "norm_after": rep.norm_after, "drift": rep.drift,
+            "bytes": rep.bytes, "apply_ms": rep.apply_ms}
+
+
+def sv_apply_gate(s: State, targets: Sequence[int], u: np.ndarray) -> None:
+    ga = GateArray([(targets, u)])
+    _check(_lib.sv_apply_gate(s.handle, ga.arr))
+
+
+def sv_norm(s: State) -> float:
+    out = ctypes.c_double()
+    _check(_lib.sv_norm(s.handle, ctypes.byref(out)))
+    return out.value
+
+
+def sv_probs(s: State, out=None):
+    """Host numpy array (float32 for C64, float64 for C128), or into a CUDA tensor."""
+    if out is not None and hasattr(out, "data_ptr"):
+        _check(_lib.sv_probs(s.handle, int(out.data_ptr()), 1))
+        return out
+    n, dt, _ = sv_info(s)
+    a = out if out is not None else np.empty(1 << n, dtype=np.float32 if dt == SV_C64 else np.float64)
+    _check(_lib.sv_probs(s.handle, a.ctypes.data, 0))
+    return a
+
+
+def sv_expect(s: State, xmask: Iterable[int], zmask: Iterable[int], coef: Iterable[float]) -> float:
+    x = np.ascontiguousarray(np.asarray(list(xmask), dtype=np.uint64))
+    z = np.ascontiguousarray(np.asarray(list(zmask), dtype=np.uint64))
+    c = np.ascontiguousarray(np.asarray(list(coef), dtype=np.float64))
+    assert x.size == z.size == c.size
+    out = ctypes.c_double()
+    u64p = ctypes.POINTER(_u64)
+    _check(_lib.sv_expect(s.handle, x.ctypes.data_as(u64p), z.ctypes.data_as(u64p), _ptr(c),
+                          x.size, ctypes.byref(out)))
+    return out.value
+
+
+def sv_topk(s: State, k: int = 64) -> Tuple[np.ndarray, np.ndarray]:
+    n, _, _ = sv_info(s)
+    m = min(k, 1 << n)
+    idx = np.zeros(k, dtype=np.uint64)
+    p = np.zeros(k, dtype=np.float64)
+    _check(_lib.sv_topk(s.handle, k, idx.ctypes.data_as(ctypes.POINTER(_u64)), _ptr(p)))
+    return idx[:m], p[:m]
+
+
+def sv_sync(s: State) -> None:
+    _check(_lib.sv_sync(s.handle))

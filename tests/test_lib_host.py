@@ -1,0 +1,112 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol, and its
+host-only entry points (gate library, sv_fuse, the precision rule, argument checks)
+agree with the oracle.  No GPU call is made here."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import gates as OG
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "sv.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sv_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(svlib):
+    lib = ctypes.CDLL(svlib.LIB_PATH)
+    declared = _declared_symbols()
+    assert len(declared) >= 19
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(declared) <= set(svlib.EXPORTS)
+
+
+def test_gate_library_matches_oracle(svlib):
+    rng = np.random.default_rng(0)
+    for name, npar in [("i", 0), ("x", 0), ("y", 0), ("z", 0), ("h", 0), ("s", 0), ("t", 0),
+                       ("rx", 1), ("ry", 1), ("rz", 1), ("u3", 3), ("sqrtx", 0), ("sqrty", 0),
+                       ("sqrtw", 0), ("cnot", 0), ("cz", 0), ("swap", 0), ("toffoli", 0),
+                       ("fsim", 2), ("cp", 1)]:
+        for dagger in (False, True):
+            p = tuple(rng.uniform(-7, 7, npar))
+            got = svlib.sv_gate_matrix(name, p, dagger)
+            want = OG.matrix(name, p, dagger)
+            assert np.max(np.abs(got - want)) < 1e-15, name
+    (spec,) = W.random_unitary_gates(5, 1, 3, rng)
+    u = OG.matrix("unitary", (), False, spec.matrix)
+    assert np.array_equal(svlib.sv_gate_matrix("unitary", matrix=spec.matrix), u)
+    assert np.array_equal(svlib.sv_gate_matrix("unitary", dagger=True, matrix=spec.matrix),
+                          u.conj().T)
+
+
+def _compare_fusion(svlib, specs, n, k):
+    want = oracle.fuse(OG.gate_list(specs), n, k)
+    c = svlib.sv_fuse(svlib.gates_from_specs(specs), n, k)
+    assert len(c) == len(want)
+    for i, (tw, uw) in enumerate(want):
+        tg, ug = svlib.sv_circuit_gate(c, i)
+        assert tg == tuple(tw), (i, tg, tw)                  # schedule: bit-exact
+        assert np.max(np.abs(ug - uw)) < 1e-12               # FP64 products
+    return len(want)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4, 5])
+def test_fusion_matches_oracle_random(svlib, k):
+    rng = np.random.default_rng(40 + k)
+    for n in (3, 6, 9):
+        _compare_fusion(svlib, W.random_unitary_gates(n, 60, 3, rng), n, k)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_fusion_matches_oracle_qft_brickwork_24q(svlib, k):
+    _, specs = W.qft_brickwork(24, 40)
+    assert len(specs) == 2192
+    _compare_fusion(svlib, specs, 24, k)
+
+
+@pytest.mark.parametrize("n,k", [(30, 4), (30, 5), (33, 5), (32, 3)])
+def test_fusion_matches_oracle_grid(svlib, n, k):
+    _compare_fusion(svlib, W.grid_random(n, 24), n, k)
+
+
+def test_fusion_matches_oracle_other_families(svlib):
+    for k in (1, 2, 3, 5):
+        _compare_fusion(svlib, W.brickwork(12, 20), 12, k)
+        _compare_fusion(svlib, W.hea(18, 6, seed=1), 18, k)
+        _compare_fusion(svlib, W.qft(20, swaps=False), 20, k)
+
+
+def test_precision_rule_matches_oracle(svlib):
+    from oracle import precision
+    for n, g, tol in [(20, 200, 1e-6), (4, 10, 1e-3), (16, 49, 1.0), (30, 1014, 1e3)]:
+        dt, e = svlib.sv_choose_dtype(n, g, tol)
+        assert e == pytest.approx(precision.eps_round(n, g), rel=1e-15)
+        assert (dt == svlib.SV_C64) == precision.choose_c64(n, g, tol)
+
+
+def test_argument_errors_are_reported(svlib):
+    h = svlib.sv_gate_matrix("h")
+    with pytest.raises(svlib.SvError) as e:
+        svlib.sv_fuse([((0, 0), np.eye(4))], 4, 2)
+    assert e.value.status == 1 and "repeated" in str(e.value)
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse([((5,), h)], 4, 2)                    # target >= n
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse([((0, 1, 2, 3, 4, 5), np.eye(64))], 8, 2)   # k > 5
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse([((0,), h)], 4, 6)                    # max_k > 5
+    with pytest.raises(svlib.SvError):
+        svlib.sv_gate_matrix("rx", ())                      # missing angle
+    with pytest.raises(svlib.SvError):
+        svlib.sv_alloc(0)                                   # n out of range, no GPU call
+    with pytest.raises(svlib.SvError):
+        svlib.sv_alloc(35)

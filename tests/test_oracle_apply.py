@@ -162,3 +162,19 @@ def test_topk_order_and_ties():
     assert list(idx) == list(range(64))
     small, _ = oracle.topk(np.array([0.1, 0.9, 0.0]), 64)    # fewer than 64 outcomes
     assert list(small) == [1, 0, 2]
+
+
+def test_probs_in_precision_and_topk_valid():
+    rng = np.random.default_rng(21)
+    psi = _rand_state(8, rng)
+    assert np.array_equal(oracle.probs_in_precision(psi), oracle.probs(psi))
+    p32 = oracle.probs_in_precision(psi.astype(np.complex64))
+    assert p32.dtype == np.float32
+    assert np.max(np.abs(p32 - oracle.probs(psi))) < 1e-6
+    p = oracle.probs(psi)
+    idx, _ = oracle.topk(p, 10)
+    assert oracle.topk_valid(idx, p, 10, 0.0)
+    bad = idx.copy()
+    bad[3] = np.argmin(p)
+    assert not oracle.topk_valid(bad, p, 10, 1e-9)
+    assert not oracle.topk_valid(np.array([idx[0], idx[0]]), p, 2, 1.0)

@@ -209,22 +209,30 @@ def table3_random(n: int, seed: Optional[int] = None) -> List[GateSpec]:
     return gates
 
 
-def random_unitary_gates(n: int, count: int, kmax: int, rng: np.random.Generator
-                         ) -> List[GateSpec]:
-    """Random dense k-qubit gates (k <= kmax) on random, unsorted distinct targets.
+def haar_unitary(d: int, rng: np.random.Generator) -> Tuple[complex, ...]:
+    """Haar-random d x d unitary: the Q factor of a complex Gaussian matrix with the
+    phases of R's diagonal folded in."""
+    z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+    q, r = np.linalg.qr(z)
+    q = q * (np.diagonal(r) / np.abs(np.diagonal(r)))
+    return tuple(complex(c) for c in q.ravel())
 
-    Each matrix is the Q factor of a complex Gaussian matrix with the phases of R's
-    diagonal folded in (Haar measure).  Used for parity cases over every target set."""
+
+def random_unitary_gates(n: int, count: int, kmax: int, rng: np.random.Generator,
+                         exact_k: bool = False, targets: Optional[Sequence[int]] = None
+                         ) -> List[GateSpec]:
+    """Random dense k-qubit gates (k <= kmax, or k = kmax with exact_k) on random,
+    unsorted distinct targets (or on the given targets, in the given order).  Used for
+    parity cases over every target set."""
     gates = []
     for _ in range(count):
-        k = int(rng.integers(1, kmax + 1))
-        k = min(k, n)
-        tg = tuple(int(t) for t in rng.choice(n, size=k, replace=False))
-        d = 1 << k
-        z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
-        q, r = np.linalg.qr(z)
-        q = q * (np.diagonal(r) / np.abs(np.diagonal(r)))
-        gates.append(GateSpec("unitary", tg, (), False, tuple(complex(c) for c in q.ravel())))
+        if targets is not None:
+            tg = tuple(int(t) for t in targets)
+        else:
+            k = kmax if exact_k else int(rng.integers(1, kmax + 1))
+            k = min(k, n)
+            tg = tuple(int(t) for t in rng.choice(n, size=k, replace=False))
+        gates.append(GateSpec("unitary", tg, (), False, haar_unitary(1 << len(tg), rng)))
     return gates
 
 
