@@ -185,6 +185,12 @@ sv_status sv_expect(sv_state *s, const uint64_t *xmask, const uint64_t *zmask,
  * descending, ties to the lower index.  idx/p are host arrays of k entries.  Synchronises. */
 sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
 
+/* Kernel selection flags for one state (default 0 = automatic: complex64 gates of width
+ * 4 and 5 on states of at least k + 7 qubits run on the tensor cores, everything else on
+ * the CUDA cores). */
+#define SV_POLICY_NO_TENSOR_CORES 1u   /* always use the CUDA-core kernels */
+sv_status sv_set_policy(sv_state *s, uint32_t flags);
+
 sv_status sv_sync(sv_state *s);   /* wait for the state's stream; reports device errors */
 const char *sv_last_error(void);  /* thread-local, never NULL */
 

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "plan.h"
 #include "ptx.cuh"
 #include "sv_internal.h"
 
@@ -142,43 +143,6 @@ constexpr uint32_t tile_bits() {
     return sizeof(R) == 4 ? (K <= 4 ? 12u : 13u) : (K <= 3 ? 11u : (K == 4 ? 12u : 13u));
 }
 
-struct Plan {
-    uint32_t L = 0, h = 0;
-    uint32_t hi[SV_MAX_K] = {0, 0, 0, 0, 0};
-    uint32_t lp[SV_MAX_K] = {0, 0, 0, 0, 0};
-    unsigned long long ntiles = 1;
-};
-
-// Largest L with L + #{targets >= L} <= TB (then equality holds); whole state if small.
-inline Plan make_plan(uint32_t n, uint32_t k, const uint32_t *t, uint32_t TB) {
-    Plan p;
-    if (n <= TB) {
-        p.L = n;
-        p.h = 0;
-    } else {
-        for (uint32_t L = TB;; --L) {
-            uint32_t h = 0;
-            for (uint32_t j = 0; j < k; ++j) h += t[j] >= L;
-            if (L + h <= TB) {
-                p.L = L;
-                p.h = h;
-                break;
-            }
-        }
-    }
-    uint32_t nh = 0;
-    for (uint32_t j = 0; j < k; ++j) {
-        if (t[j] >= p.L) {
-            p.lp[j] = p.L + nh;
-            p.hi[nh++] = t[j];
-        } else {
-            p.lp[j] = t[j];
-        }
-    }
-    p.ntiles = 1ull << (n - p.L - p.h);
-    return p;
-}
-
 template <typename R, int K>
 sv_status launch_apply_t(sv_state *s, const svi::Gate &g) {
     constexpr uint32_t TB = tile_bits<R, K>();
@@ -226,6 +190,7 @@ namespace svi {
 sv_status launch_apply(sv_state *s, const Gate &g) {
     if (g.k < 1 || g.k > SV_MAX_K || g.k > s->n)
         return set_error(SV_ERR_ARG, "apply: gate width out of range");
+    if (tc_eligible(s, g)) return launch_apply_tc(s, g);
     if (s->dtype == SV_C64) {
         switch (g.k) {
             case 1: return svk::launch_apply_t<float, 1>(s, g);

@@ -371,7 +371,7 @@ sv_status sv_probs(sv_state *s, void *out, int out_on_device) {
     clear_error();
     if (!s || !out) return set_error(SV_ERR_ARG, "sv_probs: null argument");
     if (out_on_device) return launch_probs(s, out);
-    const size_t bytes = (s->dtype == SV_C64 ? 4 : 8) << s->n;
+    const size_t bytes = size_t(s->dtype == SV_C64 ? 4 : 8) << s->n;
     void *tmp = nullptr;
     SV_CUDA(cudaMallocAsync(&tmp, bytes, s->stream));
     sv_status st = launch_probs(s, tmp);
@@ -409,6 +409,14 @@ sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
     sv_status st = launch_topk(s, k, idx, p);
     if (st != SV_OK) return st;
     return check_device_error(s);
+}
+
+sv_status sv_set_policy(sv_state *s, uint32_t flags) {
+    clear_error();
+    if (!s) return set_error(SV_ERR_ARG, "sv_set_policy: null state");
+    if (flags & ~SV_POLICY_NO_TENSOR_CORES) return set_error(SV_ERR_ARG, "sv_set_policy: unknown flag");
+    s->policy = flags;
+    return SV_OK;
 }
 
 sv_status sv_sync(sv_state *s) {

@@ -65,11 +65,14 @@ struct sv_state {
     void *snap = nullptr;       // library-owned snapshot of the initial state (c64)
     size_t snap_cap = 0;
     int num_sms = 0;
+    uint32_t policy = 0;        // SV_POLICY_* flags (kernel selection)
 };
 
 namespace svi {
 // ---- kernels (apply_kernels.cu / reduce_kernels.cu); all enqueue on s->stream ----
 sv_status launch_apply(sv_state *s, const Gate &g);
+bool tc_eligible(const sv_state *s, const Gate &g);        // apply_tc.cu
+sv_status launch_apply_tc(sv_state *s, const Gate &g);
 sv_status launch_norm(sv_state *s, double *dev_out);     // writes one double on device
 sv_status launch_probs(sv_state *s, void *dev_out);
 sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const double *c,

@@ -32,7 +32,8 @@ GATE_KINDS = {"i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "t": 6, "rx": 7, "
 EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "sv_set_state",
            "sv_get_state", "sv_fuse", "sv_circuit_free", "sv_circuit_size", "sv_circuit_gate",
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
-           "sv_expect", "sv_topk", "sv_sync", "sv_last_error"]
+           "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy"]
+SV_POLICY_NO_TENSOR_CORES = 1
 
 
 class SvError(RuntimeError):
@@ -81,6 +82,7 @@ _sig = {
     "sv_expect": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp, ctypes.c_size_t, _dp],
     "sv_topk": [_vp, _u32, ctypes.POINTER(_u64), _dp],
     "sv_sync": [_vp],
+    "sv_set_policy": [_vp, _u32],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -323,6 +325,10 @@ def sv_topk(s: State, k: int = 64) -> Tuple[np.ndarray, np.ndarray]:
     p = np.zeros(k, dtype=np.float64)
     _check(_lib.sv_topk(s.handle, k, idx.ctypes.data_as(ctypes.POINTER(_u64)), _ptr(p)))
     return idx[:m], p[:m]
+
+
+def sv_set_policy(s: State, flags: int) -> None:
+    _check(_lib.sv_set_policy(s.handle, flags))
 
 
 def sv_sync(s: State) -> None:

@@ -320,3 +320,22 @@ def test_largest_state_one_gate(gpu):
     assert np.allclose(p, 0.25, atol=1e-6)
     s.free()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_probs_to_host_30q(gpu, dtype):
+    """Probabilities of a 2^30-amplitude state copied to host memory (4 or 8 GiB)."""
+    sv = gpu
+    torch = _torch()
+    n = 30
+    x = (1 << 29) + 12345
+    s = sv.sv_alloc(n, dtype, stream=torch.cuda.current_stream())
+    sv.sv_set_basis(s, x)
+    sv.sv_apply_gate(s, (0,), OG.H)
+    p = sv.sv_probs(s)
+    assert p.size == 1 << n
+    nz = np.flatnonzero(p)
+    assert list(nz) == [x - 1, x] and np.allclose(p[nz], 0.5, atol=1e-7)
+    del p
+    s.free()
+    torch.cuda.empty_cache()
