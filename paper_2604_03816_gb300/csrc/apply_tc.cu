@@ -5,21 +5,30 @@
 // 2^{k+1} x 2^{k+1} real embedding of U
 //     R[2j][2l] = Re U[j][l],  R[2j][2l+1] = -Im U[j][l],
 //     R[2j+1][2l] = Im U[j][l], R[2j+1][2l+1] = Re U[j][l].
-// A tile of 128 groups is therefore the GEMM D[128 x N] = A[128 x K] B[N x K]^T with
-// A = the groups' amplitudes, B = R and N = K = 2^{k+1} (64 for k = 5, 32 for k = 4).
-// TF32 keeps 10 mantissa bits, too few for the complex64 accuracy target, so each
-// operand is split into TF32 parts x = x_hi + x_lo (both rounded to nearest) and
-// D = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 in tensor memory
-// (the A_lo B_lo term, of relative size 2^-22, is dropped).
+// A tile of 128 groups is the GEMM D[128 x N] = A[128 x K] B[N x K]^T with A = the
+// groups' amplitudes, B = R and N = K = 2^{k+1} (64 for k = 5, 32 for k = 4).
+//
+// Precision: the tensor cores' FP32 accumulation truncates, so a plain split of the
+// FP32 operands into TF32 parts gives errors biased toward zero (a measurable loss of
+// norm per pass).  Instead each operand is cut into three 9-bit integer slices on a
+// fixed-point grid -- per row of A (scale 2^{8-e}, e = exponent of the row's largest
+// component) and for all of B -- so that x = (a1 + a2 2^-9 + a3 2^-18) / s.  The
+// slices are exact in FP16, every product is an integer below 2^16, and the three sums
+//     D0 = A1 B1,  D1 = A1 B2 + A2 B1,  D2 = A1 B3 + A2 B2 + A3 B1
+// stay below 2^24 over K <= 64, so the tensor cores (kind::f16, FP32 accumulators in
+// TMEM) compute them exactly.  The epilogue combines them with round-to-nearest,
+// out = (D0 + (D1 + D2 2^-9) 2^-9) / (s s_B): unbiased, about FP32 accuracy relative to
+// the row's largest amplitude (the dropped slice products are below 2^-27 of it).
 //
 // Data flow of one CTA (128 threads, one group per thread, persistent over tiles):
 //   TMA 1-D bulk loads of the tile's 2^h segments into a ring of NS raw stages ->
-//   each thread gathers its group from the raw stage, splits it and writes row g of
-//   A_hi / A_lo in the K-major canonical layout -> one thread issues the 3 x K/8 MMAs
-//   into TMEM and commits them to an mbarrier -> each thread reads its row of D with
-//   tcgen05.ld and scatters the outputs back into a staging tile -> TMA bulk stores.
-// Loads of the next NS tiles are in flight while a tile is processed; the store of a
-// tile overlaps the next tile's gather.  All waits are bounded.
+//   each thread gathers its group, slices it and writes row g of A1..A3 in the K-major
+//   canonical layout (16-byte stores) -> one thread issues 6 x K/16 MMAs into three
+//   TMEM accumulators and commits them to an mbarrier -> each thread reads its row of
+//   D0..D2 with tcgen05.ld, combines and scatters the outputs into a staging tile (the
+//   A area) -> TMA bulk stores.  Loads run NS tiles ahead; a tile's store overlaps the
+//   next tile's gather.  Every wait is bounded.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,9 +44,24 @@
 namespace svk {
 
 template <int K>
+struct TcShape {
+    static constexpr uint32_t D = 1u << K;            // amplitudes per group
+    static constexpr uint32_t KD = 2u * D;            // real K = N
+    static constexpr uint32_t ROWS = 128;             // groups per tile (MMA M)
+    static constexpr uint32_t TB = K + 7;             // tile bits
+    static constexpr uint32_t TILE_BYTES = ROWS * D * 8u;
+    static constexpr uint32_t A_BYTES = ROWS * KD * 2u;   // one FP16 slice of A
+    static constexpr uint32_t B_BYTES = KD * KD * 2u;     // one FP16 slice of B
+    static constexpr uint32_t SBO = (KD / 8u) * 128u;     // 8-row group stride
+    static constexpr uint32_t NS = 4;                     // raw stages
+    static constexpr uint32_t SMEM = 3u * B_BYTES + 3u * A_BYTES + NS * TILE_BYTES;
+    static constexpr uint32_t TMEM_COLS = K == 5 ? 256u : 128u;   // 3 accumulators of KD
+};
+
+template <int K>
 struct TcArgs {
-    // U split into TF32 parts on the host from the FP64 matrix, row-major.
-    float uhr[1 << (2 * K)], uhi[1 << (2 * K)], ulr[1 << (2 * K)], uli[1 << (2 * K)];
+    int16_t b[3][(2u << K) * (2u << K)];   // slices of R (row-major n x kk), |b| <= 256
+    float b_inv_scale;                     // R = (b1 + b2 2^-9 + b3 2^-18) * b_inv_scale
     void *psi;
     int *err;
     unsigned long long ntiles;
@@ -46,19 +70,10 @@ struct TcArgs {
     uint32_t lp[K];
 };
 
-template <int K>
-struct TcShape {
-    static constexpr uint32_t D = 1u << K;            // amplitudes per group
-    static constexpr uint32_t KD = 2u * D;            // real K = N
-    static constexpr uint32_t ROWS = 128;             // groups per tile (MMA M)
-    static constexpr uint32_t TB = K + 7;             // tile bits
-    static constexpr uint32_t TILE_BYTES = ROWS * D * 8u;
-    static constexpr uint32_t A_BYTES = ROWS * KD * 4u;   // == TILE_BYTES
-    static constexpr uint32_t B_BYTES = KD * KD * 4u;
-    static constexpr uint32_t SBO = (KD / 4u) * 128u;     // 8-row group stride
-    static constexpr uint32_t NS = K == 5 ? 3u : 4u;      // raw stages
-    static constexpr uint32_t SMEM = 2u * B_BYTES + 2u * A_BYTES + NS * TILE_BYTES;
-};
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);   // exact: |a|, |b| <= 256 are integers
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
 
 template <int K>
 __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
@@ -68,12 +83,11 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
     __shared__ __align__(8) unsigned long long full[NS];
     __shared__ __align__(8) unsigned long long mma_bar;
     __shared__ uint32_t tmem_slot;
-    // B first, so that operand reads stay inside the CTA's shared memory whatever the
-    // descriptor strides.
-    unsigned char *sBh = smem, *sBl = smem + S::B_BYTES;
-    unsigned char *sAh = smem + 2 * S::B_BYTES, *sAl = sAh + S::A_BYTES;
-    float2 *raw0 = reinterpret_cast<float2 *>(sAl + S::A_BYTES);
-    float2 *stage_out = reinterpret_cast<float2 *>(sAh);   // outputs reuse A_hi
+    // B slices first, then A slices, then the raw stages: operand reads stay inside the
+    // CTA's shared memory whatever the descriptor strides.
+    unsigned char *sB = smem, *sA = smem + 3 * S::B_BYTES;
+    float2 *raw0 = reinterpret_cast<float2 *>(sA + 3 * S::A_BYTES);
+    float2 *stage_out = reinterpret_cast<float2 *>(sA);   // outputs reuse the A area
     float2 *psi = reinterpret_cast<float2 *>(a.psi);
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
 
@@ -81,9 +95,8 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
     const uint32_t seg_bytes = seg_amps * 8u;
     const uint32_t nseg = 1u << a.h;
 
-    // ---- set-up: TMEM, barriers, B = R split into TF32 parts
     if (warp == 0) {
-        tmem_alloc(smem_u32(&tmem_slot), KD);
+        tmem_alloc(smem_u32(&tmem_slot), S::TMEM_COLS);
         tmem_relinquish();
     }
     if (tid == 0) {
@@ -92,19 +105,10 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
         fence_mbar_init();
     }
     for (uint32_t e = tid; e < KD * KD; e += blockDim.x) {
-        const uint32_t n = e / KD, kk = e % KD;
-        const uint32_t j = n >> 1, l = kk >> 1, u = j * D + l;
-        float vh, vl;
-        if ((n & 1) == (kk & 1)) {                  // Re U on the diagonal of the 2x2 block
-            vh = a.uhr[u]; vl = a.ulr[u];
-        } else if (n & 1) {                         // R[2j+1][2l] = Im U
-            vh = a.uhi[u]; vl = a.uli[u];
-        } else {                                    // R[2j][2l+1] = -Im U
-            vh = -a.uhi[u]; vl = -a.uli[u];
-        }
-        const uint32_t off = kmajor_off(n, kk, S::SBO);
-        *reinterpret_cast<float *>(sBh + off) = vh;
-        *reinterpret_cast<float *>(sBl + off) = vl;
+        const uint32_t n = e / KD, kk = e % KD, off = kmajor_off16(n, kk, S::SBO);
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            *reinterpret_cast<__half *>(sB + j * S::B_BYTES + off) = __int2half_rn(a.b[j][e]);
     }
     uint32_t coff[D];
 #pragma unroll
@@ -123,24 +127,26 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = idesc_tf32(S::ROWS, KD);
+    const uint32_t idesc = idesc_f16(S::ROWS, KD);
 
     auto tile_base = [&](unsigned long long t) {
         unsigned long long base = t << a.L;
         for (uint32_t j = 0; j < a.h; ++j) base = insert_zero64(base, a.hi[j]);
         return base;
     };
+    auto seg_off = [&](unsigned long long base, uint32_t sg) {
+        unsigned long long off = base;
+        for (uint32_t j = 0; j < a.h; ++j)
+            if ((sg >> j) & 1u) off |= 1ull << a.hi[j];
+        return off;
+    };
     auto issue_load = [&](unsigned long long t, uint32_t s) {
         const unsigned long long base = tile_base(t);
         const uint32_t bar = smem_u32(&full[s]);
         mbar_arrive_expect_tx(bar, S::TILE_BYTES);
         float2 *dst = raw0 + (size_t)s * (S::TILE_BYTES / 8u);
-        for (uint32_t sg = 0; sg < nseg; ++sg) {
-            unsigned long long off = base;
-            for (uint32_t j = 0; j < a.h; ++j)
-                if ((sg >> j) & 1u) off |= 1ull << a.hi[j];
-            bulk_g2s(smem_u32(dst + (size_t)sg * seg_amps), psi + off, seg_bytes, bar);
-        }
+        for (uint32_t sg = 0; sg < nseg; ++sg)
+            bulk_g2s(smem_u32(dst + (size_t)sg * seg_amps), psi + seg_off(base, sg), seg_bytes, bar);
     };
 
     const unsigned long long first = blockIdx.x, step = gridDim.x;
@@ -155,35 +161,64 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
     for (unsigned long long t = first; t < a.ntiles; t += step, ++it) {
         const uint32_t s = it % NS;
         const uint32_t par = (it / NS) & 1u;
-        if (tid == 0) bulk_wait_read_all();          // previous tile's store left A_hi
+        if (tid == 0) bulk_wait_read_all();          // previous tile's store left the A area
         const bool ok = mbar_wait_bounded(smem_u32(&full[s]), par);
         if (!__syncthreads_and(ok)) { failed = true; break; }
 
-        // gather this thread's group, split into TF32 parts, write row `tid` of A
+        // gather this thread's group and cut it into three 9-bit integer slices
         const float2 *rs = raw0 + (size_t)s * (S::TILE_BYTES / 8u);
-#pragma unroll 8
+        float2 v[D];
+        float m = 0.f;
+#pragma unroll
         for (uint32_t c = 0; c < D; ++c) {
-            const float2 v = rs[gbase | coff[c]];
-            const float hr = tf32_rna(v.x), hi = tf32_rna(v.y);
-            const float lr = tf32_rna(v.x - hr), li = tf32_rna(v.y - hi);
-            const uint32_t off = kmajor_off(tid, 2 * c, S::SBO);
-            *reinterpret_cast<float2 *>(sAh + off) = make_float2(hr, hi);
-            *reinterpret_cast<float2 *>(sAl + off) = make_float2(lr, li);
+            v[c] = rs[gbase | coff[c]];
+            m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
+        }
+        int ex = 0;
+        frexpf(m, &ex);                              // m < 2^ex (m = 0: ex = 0)
+        ex = max(ex, -100);                          // keep 2^(8-ex) finite
+        const float scale = ldexpf(1.f, 8 - ex);     // |x * scale| < 256
+        const float out_scale = ldexpf(a.b_inv_scale, ex - 8);
+#pragma unroll
+        for (uint32_t q = 0; q < D / 4; ++q) {       // 4 amplitudes = 16 bytes per slice
+            uint32_t w[3][4];
+#pragma unroll
+            for (uint32_t i = 0; i < 4; ++i) {
+                const float2 x = v[4 * q + i];
+                const float xr = x.x * scale, xi = x.y * scale;
+                const float r1 = rintf(xr), i1 = rintf(xi);
+                const float xr2 = (xr - r1) * 512.f, xi2 = (xi - i1) * 512.f;
+                const float r2 = rintf(xr2), i2 = rintf(xi2);
+                const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
+                w[0][i] = pack_half2(r1, i1);
+                w[1][i] = pack_half2(r2, i2);
+                w[2][i] = pack_half2(r3, i3);
+            }
+            const uint32_t off = kmajor_off16(tid, 8 * q, S::SBO);
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                *reinterpret_cast<uint4 *>(sA + j * S::A_BYTES + off) =
+                    make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
         }
         fence_proxy_async_smem();
         __syncthreads();
 
         if (tid == 0) {
             tc_fence_after();
-            const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl);
-            const uint32_t bh = smem_u32(sBh), bl = smem_u32(sBl);
+            const uint32_t A0 = smem_u32(sA), B0 = smem_u32(sB);
+            // (accumulator, A slice, B slice) for D0 = A1B1, D1 = A1B2 + A2B1,
+            // D2 = A1B3 + A2B2 + A3B1
+            const uint32_t prod[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
 #pragma unroll
-            for (uint32_t p = 0; p < 3; ++p) {
-                const uint32_t A = p == 2 ? al : ah, B = p == 1 ? bl : bh;
+            for (int p = 0; p < 6; ++p) {
+                const uint32_t acc = prod[p][0];
+                const uint32_t Aa = A0 + prod[p][1] * S::A_BYTES, Bb = B0 + prod[p][2] * S::B_BYTES;
+                const bool first_in_acc = (p == 0 || p == 1 || p == 3);
 #pragma unroll
-                for (uint32_t ks = 0; ks < KD / 8; ++ks)
-                    mma_tf32(tmem, smem_desc(A + ks * 256u, 128u, S::SBO),
-                             smem_desc(B + ks * 256u, 128u, S::SBO), idesc, (p | ks) != 0);
+                for (uint32_t ks = 0; ks < KD / 16; ++ks)
+                    mma_f16(tmem + acc * KD, smem_desc(Aa + ks * 256u, 128u, S::SBO),
+                            smem_desc(Bb + ks * 256u, 128u, S::SBO), idesc,
+                            (first_in_acc && ks == 0) ? 0u : 1u);
             }
             mma_commit(smem_u32(&mma_bar));
             const unsigned long long nt = t + NS * step;   // raw stage s is free again
@@ -193,29 +228,28 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
         if (!__syncthreads_and(ok2)) { failed = true; break; }
         tc_fence_after();
 
-        // row `tid` of D: outputs of this thread's group, scattered into the staging tile
-        float d[KD];
+        // row `tid` of D0..D2 -> outputs of this thread's group -> staging tile
+        const uint32_t lane_addr = tmem + ((warp * 32u) << 16);
 #pragma unroll
         for (uint32_t c0 = 0; c0 < KD; c0 += 32) {
-            float part[32];
-            tmem_ld32(tmem + ((warp * 32u) << 16) + c0, part);
+            float d0[32], d1[32], d2[32];
+            tmem_ld32(lane_addr + c0, d0);
+            tmem_ld32(lane_addr + KD + c0, d1);
+            tmem_ld32(lane_addr + 2 * KD + c0, d2);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) d[c0 + i] = part[i];
+            for (uint32_t i = 0; i < 32; i += 2) {
+                const float re = (d0[i] + (d1[i] + d2[i] * (1.f / 512.f)) * (1.f / 512.f)) * out_scale;
+                const float im = (d0[i + 1] + (d1[i + 1] + d2[i + 1] * (1.f / 512.f)) * (1.f / 512.f)) * out_scale;
+                stage_out[gbase | coff[(c0 + i) / 2]] = make_float2(re, im);
+            }
         }
-        tmem_wait_ld();
-#pragma unroll
-        for (uint32_t c = 0; c < D; ++c) stage_out[gbase | coff[c]] = make_float2(d[2 * c], d[2 * c + 1]);
         fence_proxy_async_smem();
         tc_fence_before();
         __syncthreads();
         if (tid == 0) {
             const unsigned long long base = tile_base(t);
-            for (uint32_t sg = 0; sg < nseg; ++sg) {
-                unsigned long long off = base;
-                for (uint32_t j = 0; j < a.h; ++j)
-                    if ((sg >> j) & 1u) off |= 1ull << a.hi[j];
-                bulk_s2g(psi + off, smem_u32(stage_out + (size_t)sg * seg_amps), seg_bytes);
-            }
+            for (uint32_t sg = 0; sg < nseg; ++sg)
+                bulk_s2g(psi + seg_off(base, sg), smem_u32(stage_out + (size_t)sg * seg_amps), seg_bytes);
             bulk_commit();
         }
     }
@@ -223,26 +257,13 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
     if (tid == 0) bulk_wait_all();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, KD);
-}
-
-// Host: round to TF32 (10 mantissa bits), nearest with ties away from zero, like
-// cvt.rna.tf32.f32.
-static float tf32_host(float x) {
-    uint32_t b;
-    std::memcpy(&b, &x, 4);
-    if ((b & 0x7F800000u) != 0x7F800000u) {
-        b += 0x1000u;
-        b &= ~0x1FFFu;
-    }
-    float r;
-    std::memcpy(&r, &b, 4);
-    return r;
+    if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 template <int K>
 sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     using S = TcShape<K>;
+    constexpr uint32_t D = S::D, KD = S::KD;
     static std::once_flag once;
     static cudaError_t init_err = cudaSuccess;
     std::call_once(once, [] {
@@ -254,13 +275,28 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
                                                cudaGetErrorString(init_err));
     const Plan p = make_plan(s->n, K, g.t, S::TB);
     TcArgs<K> a;
-    for (int i = 0; i < (1 << (2 * K)); ++i) {
-        const double re = g.u[i].real(), im = g.u[i].imag();
-        a.uhr[i] = tf32_host((float)re);
-        a.uhi[i] = tf32_host((float)im);
-        a.ulr[i] = tf32_host((float)(re - (double)a.uhr[i]));
-        a.uli[i] = tf32_host((float)(im - (double)a.uhi[i]));
-    }
+    // R (real embedding of U) and its fixed-point slices, in FP64 on the host
+    double rmax = 0.0;
+    for (uint32_t i = 0; i < D * D; ++i)
+        rmax = std::max(rmax, std::max(std::fabs(g.u[i].real()), std::fabs(g.u[i].imag())));
+    int eb = 0;
+    std::frexp(rmax, &eb);                                   // rmax < 2^eb
+    const double sb = std::ldexp(1.0, 8 - eb);
+    for (uint32_t n = 0; n < KD; ++n)
+        for (uint32_t kk = 0; kk < KD; ++kk) {
+            const svi::cplx u = g.u[(n >> 1) * D + (kk >> 1)];
+            double r = ((n & 1) == (kk & 1)) ? u.real() : ((n & 1) ? u.imag() : -u.imag());
+            double x = r * sb;
+            const double b1 = std::nearbyint(x);
+            x = (x - b1) * 512.0;
+            const double b2 = std::nearbyint(x);
+            x = (x - b2) * 512.0;
+            const double b3 = std::nearbyint(x);
+            a.b[0][n * KD + kk] = (int16_t)b1;
+            a.b[1][n * KD + kk] = (int16_t)b2;
+            a.b[2][n * KD + kk] = (int16_t)b3;
+        }
+    a.b_inv_scale = (float)std::ldexp(1.0, eb - 8);
     a.psi = s->buf;
     a.err = reinterpret_cast<int *>(s->ws + svi::WS_ERR);
     a.ntiles = p.ntiles;
