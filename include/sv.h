@@ -191,6 +191,25 @@ sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
 #define SV_POLICY_NO_TENSOR_CORES 1u   /* always use the CUDA-core kernels */
 sv_status sv_set_policy(sv_state *s, uint32_t flags);
 
+/* sum_t coef[t] <psi| P_t |psi> (as sv_expect) for a caller-owned device state, written
+ * to out_dev (one double in device memory), enqueued on `stream` (NULL = the legacy
+ * default stream) -- without allocating anything.  No counterpart in the paper: it
+ * exists for callers that cannot call cudaMalloc or cudaFree, such as code running
+ * inside a global-mode CUDA stream capture, a host framework that owns the whole
+ * device-memory budget, or a latency-critical loop that must not synchronise the device.
+ *   psi: 2^n amplitudes in dtype, 16-byte aligned device memory; n in 1..34.
+ * Scratch: a fixed 128 KiB device array inside the library (one FP64 partial per block
+ * for each batch of up to 32 terms sharing an X-part; at most 64 batches, else
+ * SV_ERR_ARG).  Every GPU that loads the library holds it until the process exits.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one array, so
+ * calls whose work overlaps on the GPU (different streams, no ordering) race; calls on
+ * one stream are ordered.  Every scratch slot a call reads is written earlier in the same
+ * call, so stale contents from a previous call are never used.  Asynchronous. */
+sv_status sv_expect_noalloc(const void *psi, uint32_t n, sv_dtype dtype, const uint64_t *xmask,
+                            const uint64_t *zmask, const double *coef, size_t nterms,
+                            double *out_dev, void *stream);
+
 sv_status sv_sync(sv_state *s);   /* wait for the state's stream; reports device errors */
 const char *sv_last_error(void);  /* thread-local, never NULL */
 

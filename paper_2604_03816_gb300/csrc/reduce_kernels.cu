@@ -410,6 +410,66 @@ sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
     return SV_OK;
 }
 
+// Enqueue sum_t coef[t] <P_t> for a raw device state into *out_dev, with block partials
+// in caller-provided scratch (nb_fixed doubles per batch of up to EXP_MAX_TERMS terms
+// sharing one X-part).  Uses no heap memory: the term order lives on the stack, so
+// nterms is limited to ENQ_MAX_TERMS.  SV_ERR_ARG if the batches need more scratch.
+sv_status enqueue_expect_sum(const void *psi, uint32_t n, sv_dtype dtype, const uint64_t *x,
+                             const uint64_t *z, const double *c, size_t nterms, double *scratch,
+                             size_t scratch_doubles, int nb_fixed, double *out_dev,
+                             cudaStream_t stream) {
+    constexpr size_t ENQ_MAX_TERMS = 2048;
+    if (nterms > ENQ_MAX_TERMS)
+        return set_error(SV_ERR_ARG, "expectation: at most 2048 terms per call");
+    if (nterms == 0) {
+        SV_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(double), stream));
+        return SV_OK;
+    }
+    uint16_t order[ENQ_MAX_TERMS];
+    for (size_t i = 0; i < nterms; ++i) {          // stable insertion sort by X-part
+        size_t j = i;
+        while (j > 0 && x[order[j - 1]] > x[i]) {
+            order[j] = order[j - 1];
+            --j;
+        }
+        order[j] = (uint16_t)i;
+    }
+    size_t nbatches = 0;
+    for (size_t i = 0, run = 0; i < nterms; ++i) {
+        run = (i > 0 && x[order[i]] == x[order[i - 1]]) ? run + 1 : 0;
+        if (run % svk::EXP_MAX_TERMS == 0) ++nbatches;
+    }
+    if (nbatches * (size_t)nb_fixed > scratch_doubles)
+        return set_error(SV_ERR_ARG, "expectation: too many term batches for the scratch array");
+    size_t i = 0, b = 0;
+    while (i < nterms) {
+        svk::ExpectArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.x = x[order[i]];
+        while (i < nterms && x[order[i]] == a.x && a.nterms < svk::EXP_MAX_TERMS) {
+            const size_t t = order[i++];
+            const int y = __builtin_popcountll(a.x & z[t]) & 3;
+            const double re[4] = {1, 0, -1, 0}, im[4] = {0, 1, 0, -1};
+            a.z[a.nterms] = z[t];
+            a.ccr[a.nterms] = c[t] * re[y];
+            a.cci[a.nterms] = c[t] * im[y];
+            ++a.nterms;
+        }
+        a.hb = a.x ? 63 - __builtin_clzll(a.x) : 0;
+        a.npairs = a.x ? (1ull << (n - 1)) : (1ull << n);
+        double *part = scratch + (b++) * (size_t)nb_fixed;
+        if (dtype == SV_C64)
+            svk::expect_kernel<float><<<nb_fixed, svk::RED_THREADS, 0, stream>>>(a, psi, part);
+        else
+            svk::expect_kernel<double><<<nb_fixed, svk::RED_THREADS, 0, stream>>>(a, psi, part);
+        SV_CUDA(cudaGetLastError());
+    }
+    svk::sum_partials<<<1, svk::RED_THREADS, 0, stream>>>(scratch, (int)(nbatches * nb_fixed),
+                                                          out_dev);
+    SV_CUDA(cudaGetLastError());
+    return SV_OK;
+}
+
 sv_status launch_widen(sv_state *s, const void *src_c64, void *dst_c128) {
     const unsigned long long N = 1ull << s->n;
     svk::widen_kernel<<<s->num_sms * 8, 256, 0, s->stream>>>(

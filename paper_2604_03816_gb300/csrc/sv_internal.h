@@ -81,6 +81,10 @@ sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
 sv_status launch_widen(sv_state *s, const void *src_c64, void *dst_c128);
 sv_status launch_set_one(sv_state *s, uint64_t x);
 sv_status check_device_error(sv_state *s);   // synchronises; reads and clears the error word
+sv_status enqueue_expect_sum(const void *psi, uint32_t n, sv_dtype dtype, const uint64_t *x,
+                             const uint64_t *z, const double *c, size_t nterms, double *scratch,
+                             size_t scratch_doubles, int nb_fixed, double *out_dev,
+                             cudaStream_t stream);
 }  // namespace svi
 
 #define SV_CUDA(call)                                                                    \

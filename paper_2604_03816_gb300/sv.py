@@ -32,7 +32,8 @@ GATE_KINDS = {"i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "t": 6, "rx": 7, "
 EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "sv_set_state",
            "sv_get_state", "sv_fuse", "sv_circuit_free", "sv_circuit_size", "sv_circuit_gate",
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
-           "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy"]
+           "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
+           "sv_expect_noalloc"]
 SV_POLICY_NO_TENSOR_CORES = 1
 
 
@@ -83,6 +84,8 @@ _sig = {
     "sv_topk": [_vp, _u32, ctypes.POINTER(_u64), _dp],
     "sv_sync": [_vp],
     "sv_set_policy": [_vp, _u32],
+    "sv_expect_noalloc": [_vp, _u32, _i32, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp,
+                          ctypes.c_size_t, _vp, _vp],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -316,6 +319,21 @@ def sv_expect(s: State, xmask: Iterable[int], zmask: Iterable[int], coef: Iterab
     _check(_lib.sv_expect(s.handle, x.ctypes.data_as(u64p), z.ctypes.data_as(u64p), _ptr(c),
                           x.size, ctypes.byref(out)))
     return out.value
+
+
+def sv_expect_noalloc(psi, n: int, dtype: int, xmask: Iterable[int], zmask: Iterable[int],
+                      coef: Iterable[float], out, stream=None) -> None:
+    """psi: CUDA tensor (or device pointer) holding the state; out: CUDA float64 tensor
+    (or device pointer) receiving sum_t c_t <P_t>.  Asynchronous; allocates nothing."""
+    x = np.ascontiguousarray(np.asarray(list(xmask), dtype=np.uint64))
+    z = np.ascontiguousarray(np.asarray(list(zmask), dtype=np.uint64))
+    c = np.ascontiguousarray(np.asarray(list(coef), dtype=np.float64))
+    assert x.size == z.size == c.size
+    pp = int(psi.data_ptr()) if hasattr(psi, "data_ptr") else int(psi)
+    op = int(out.data_ptr()) if hasattr(out, "data_ptr") else int(out)
+    u64p = ctypes.POINTER(_u64)
+    _check(_lib.sv_expect_noalloc(pp, n, dtype, x.ctypes.data_as(u64p), z.ctypes.data_as(u64p),
+                                  _ptr(c), x.size, op, _stream_ptr(stream)))
 
 
 def sv_topk(s: State, k: int = 64) -> Tuple[np.ndarray, np.ndarray]:
