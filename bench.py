@@ -233,6 +233,8 @@ def main():
 
     def step(timing=False):
         c = sv.sv_fuse(gates, args.n, args.k)
+        if sv.sv_info(state)[1] != dt:           # a promotion widened the state last time
+            sv.sv_set_dtype(state, dt)
         sv.sv_set_basis(state, 0)
         rep = sv.sv_apply_circuit(state, c, adaptive=True, timing=timing)
         idx, p = sv.sv_topk(state, 64)
@@ -282,8 +284,7 @@ def main():
             traffic = TRAFFIC["bytes_per_launch"]
 
         if sv.sv_info(state)[1] != dt:          # a promotion widened the state: start over
-            state.free()
-            state = sv.sv_alloc(args.n, dt, stream=stream)
+            sv.sv_set_dtype(state, dt)
         # end to end through the C ABI with host buffers: the initial state in from pinned
         # host memory, all 2^n probabilities out to pinned host memory, every step
         e2e = None
@@ -300,6 +301,8 @@ def main():
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(stream)
             for _ in range(args.e2e_steps):
+                if sv.sv_info(state)[1] != dt:
+                    sv.sv_set_dtype(state, dt)
                 sv.sv_set_state(state, h_in_np)
                 c = sv.sv_fuse(gates, args.n, args.k)
                 sv.sv_apply_circuit(state, c, adaptive=True)

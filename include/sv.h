@@ -104,6 +104,11 @@ sv_status sv_info(const sv_state *s, uint32_t *n, sv_dtype *dtype, void **dev_pt
 
 /* |x> (x < 2^n).  Asynchronous. */
 sv_status sv_set_basis(sv_state *s, uint64_t x);
+/* Change the state's precision (e.g. back to SV_C64 after a promotion).  The contents
+ * become |0...0> in the new dtype.  A library-owned buffer is reallocated when it is too
+ * small; a caller buffer must already hold 2^n amplitudes of the new dtype (else
+ * SV_ERR_STATE). */
+sv_status sv_set_dtype(sv_state *s, sv_dtype dtype);
 /* Copy 2^n amplitudes in the state's dtype from src (host or device memory).  Host
  * sources are copied synchronously; pinned host memory is fastest. */
 sv_status sv_set_state(sv_state *s, const void *src, int src_on_device);

@@ -20,14 +20,18 @@
 // out = (D0 + (D1 + D2 2^-9) 2^-9) / (s s_B): unbiased, about FP32 accuracy relative to
 // the row's largest amplitude (the dropped slice products are below 2^-27 of it).
 //
-// Data flow of one CTA (128 threads, one group per thread, persistent over tiles):
-//   TMA 1-D bulk loads of the tile's 2^h segments into a ring of NS raw stages ->
-//   each thread gathers its group, slices it and writes row g of A1..A3 in the K-major
-//   canonical layout (16-byte stores) -> one thread issues 6 x K/16 MMAs into three
-//   TMEM accumulators and commits them to an mbarrier -> each thread reads its row of
-//   D0..D2 with tcgen05.ld, combines and scatters the outputs into a staging tile (the
-//   A area) -> TMA bulk stores.  Loads run NS tiles ahead; a tile's store overlaps the
-//   next tile's gather.  Every wait is bounded.
+// One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
+//   warp 4 (one thread)  TMA producer: 1-D bulk loads of each tile's 2^h segments into a
+//                        ring of NS raw stages;
+//   warps 0-3            transform: one group (row of A) per thread -- gather from the
+//                        raw stage, cut into three 9-bit slices, 16-byte stores into the
+//                        K-major canonical layout of A (double-buffered);
+//   warp 5 (one thread)  MMA issuer: 6 x K/16 tcgen05.mma.kind::f16 into three TMEM
+//                        accumulators (double-buffered), committed to mbarriers;
+//   warps 6-9            epilogue: tcgen05.ld of their 32-lane quadrant, combine, scatter
+//                        into an output staging tile, TMA bulk stores.
+// So loads, slicing, MMAs and stores of consecutive tiles overlap.  Every wait is
+// bounded and any role that gives up makes the others leave too (abort flag).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -53,9 +57,15 @@ struct TcShape {
     static constexpr uint32_t A_BYTES = ROWS * KD * 2u;   // one FP16 slice of A
     static constexpr uint32_t B_BYTES = KD * KD * 2u;     // one FP16 slice of B
     static constexpr uint32_t SBO = (KD / 8u) * 128u;     // 8-row group stride
-    static constexpr uint32_t NS = 4;                     // raw stages
-    static constexpr uint32_t SMEM = 3u * B_BYTES + 3u * A_BYTES + NS * TILE_BYTES;
-    static constexpr uint32_t TMEM_COLS = K == 5 ? 256u : 128u;   // 3 accumulators of KD
+    static constexpr uint32_t NS = K == 5 ? 2u : 4u;      // raw stages
+    static constexpr uint32_t NOUT = K == 5 ? 1u : 2u;    // output staging buffers
+    static constexpr uint32_t ACC = 3u * KD;              // TMEM columns of one D set
+    static constexpr uint32_t TMEM_COLS = K == 5 ? 512u : 256u;   // two D sets
+    static constexpr uint32_t OFF_A = 3u * B_BYTES;
+    static constexpr uint32_t OFF_RAW = OFF_A + 2u * 3u * A_BYTES;
+    static constexpr uint32_t OFF_OUT = OFF_RAW + NS * TILE_BYTES;
+    static constexpr uint32_t SMEM = OFF_OUT + NOUT * TILE_BYTES;
+    static constexpr uint32_t THREADS = 320;              // 10 warps
 };
 
 template <int K>
@@ -76,32 +86,43 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
 }
 
 template <int K>
-__global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
+__global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
     using S = TcShape<K>;
-    constexpr uint32_t D = S::D, KD = S::KD, NS = S::NS;
+    constexpr uint32_t D = S::D, KD = S::KD, NS = S::NS, NOUT = S::NOUT;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) unsigned long long full[NS];
-    __shared__ __align__(8) unsigned long long mma_bar;
+    __shared__ __align__(8) unsigned long long full[NS], empty[NS];
+    __shared__ __align__(8) unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2];
+    __shared__ __align__(8) unsigned long long scale_full[4];   // row scales, tile j -> j & 3
+    __shared__ float row_scale[4][128];
     __shared__ uint32_t tmem_slot;
-    // B slices first, then A slices, then the raw stages: operand reads stay inside the
-    // CTA's shared memory whatever the descriptor strides.
-    unsigned char *sB = smem, *sA = smem + 3 * S::B_BYTES;
-    float2 *raw0 = reinterpret_cast<float2 *>(sA + 3 * S::A_BYTES);
-    float2 *stage_out = reinterpret_cast<float2 *>(sA);   // outputs reuse the A area
+    __shared__ int abort_flag;
+    // B slices, then two sets of A slices, the raw stages and the output staging tiles;
+    // operand reads stay inside the CTA's shared memory whatever the descriptor strides.
+    unsigned char *sB = smem;
     float2 *psi = reinterpret_cast<float2 *>(a.psi);
-    const uint32_t tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     const uint32_t seg_amps = 1u << a.L;
     const uint32_t seg_bytes = seg_amps * 8u;
     const uint32_t nseg = 1u << a.h;
 
-    if (warp == 0) {
+    if (warp == 5) {
         tmem_alloc(smem_u32(&tmem_slot), S::TMEM_COLS);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (uint32_t s = 0; s < NS; ++s) mbar_init(smem_u32(&full[s]), 1);
-        mbar_init(smem_u32(&mma_bar), 1);
+        for (uint32_t s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&a_full[b]), 1);
+            mbar_init(smem_u32(&a_empty[b]), 1);
+            mbar_init(smem_u32(&d_full[b]), 1);
+            mbar_init(smem_u32(&d_empty[b]), 1);
+        }
+        for (int q = 0; q < 4; ++q) mbar_init(smem_u32(&scale_full[q]), 1);
+        abort_flag = 0;
         fence_mbar_init();
     }
     for (uint32_t e = tid; e < KD * KD; e += blockDim.x) {
@@ -110,24 +131,13 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
         for (int j = 0; j < 3; ++j)
             *reinterpret_cast<__half *>(sB + j * S::B_BYTES + off) = __int2half_rn(a.b[j][e]);
     }
-    uint32_t coff[D];
-#pragma unroll
-    for (uint32_t c = 0; c < D; ++c) {
-        uint32_t o = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if ((c >> j) & 1) o |= 1u << a.lp[j];
-        coff[c] = o;
-    }
-    uint32_t gbase = tid;                           // this thread's group base in the tile
-#pragma unroll
-    for (int j = 0; j < K; ++j) gbase = insert_zero32(gbase, a.lp[j]);
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = idesc_f16(S::ROWS, KD);
+    volatile int *abort = &abort_flag;
+    const unsigned long long first = blockIdx.x, step = gridDim.x;
 
     auto tile_base = [&](unsigned long long t) {
         unsigned long long base = t << a.L;
@@ -140,124 +150,183 @@ __global__ void __launch_bounds__(128, 1) apply_tc(const __grid_constant__ TcArg
             if ((sg >> j) & 1u) off |= 1ull << a.hi[j];
         return off;
     };
-    auto issue_load = [&](unsigned long long t, uint32_t s) {
-        const unsigned long long base = tile_base(t);
-        const uint32_t bar = smem_u32(&full[s]);
-        mbar_arrive_expect_tx(bar, S::TILE_BYTES);
-        float2 *dst = raw0 + (size_t)s * (S::TILE_BYTES / 8u);
-        for (uint32_t sg = 0; sg < nseg; ++sg)
-            bulk_g2s(smem_u32(dst + (size_t)sg * seg_amps), psi + seg_off(base, sg), seg_bytes, bar);
+    auto group_base = [&](uint32_t row) {
+        uint32_t g = row;
+#pragma unroll
+        for (int j = 0; j < K; ++j) g = insert_zero32(g, a.lp[j]);
+        return g;
     };
-
-    const unsigned long long first = blockIdx.x, step = gridDim.x;
-    if (tid == 0)
-        for (uint32_t s = 0; s < NS; ++s) {
-            const unsigned long long t = first + s * step;
-            if (t < a.ntiles) issue_load(t, s);
-        }
-
-    bool failed = false;
-    uint32_t it = 0;
-    for (unsigned long long t = first; t < a.ntiles; t += step, ++it) {
-        const uint32_t s = it % NS;
-        const uint32_t par = (it / NS) & 1u;
-        if (tid == 0) bulk_wait_read_all();          // previous tile's store left the A area
-        const bool ok = mbar_wait_bounded(smem_u32(&full[s]), par);
-        if (!__syncthreads_and(ok)) { failed = true; break; }
-
-        // gather this thread's group and cut it into three 9-bit integer slices
-        const float2 *rs = raw0 + (size_t)s * (S::TILE_BYTES / 8u);
-        float2 v[D];
-        float m = 0.f;
+    auto member_offsets = [&](uint32_t (&coff)[D]) {
 #pragma unroll
         for (uint32_t c = 0; c < D; ++c) {
-            v[c] = rs[gbase | coff[c]];
-            m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
+            uint32_t o = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                if ((c >> j) & 1) o |= 1u << a.lp[j];
+            coff[c] = o;
         }
-        int ex = 0;
-        frexpf(m, &ex);                              // m < 2^ex (m = 0: ex = 0)
-        ex = max(ex, -100);                          // keep 2^(8-ex) finite
-        const float scale = ldexpf(1.f, 8 - ex);     // |x * scale| < 256
-        const float out_scale = ldexpf(a.b_inv_scale, ex - 8);
-#pragma unroll
-        for (uint32_t q = 0; q < D / 4; ++q) {       // 4 amplitudes = 16 bytes per slice
-            uint32_t w[3][4];
-#pragma unroll
-            for (uint32_t i = 0; i < 4; ++i) {
-                const float2 x = v[4 * q + i];
-                const float xr = x.x * scale, xi = x.y * scale;
-                const float r1 = rintf(xr), i1 = rintf(xi);
-                const float xr2 = (xr - r1) * 512.f, xi2 = (xi - i1) * 512.f;
-                const float r2 = rintf(xr2), i2 = rintf(xi2);
-                const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
-                w[0][i] = pack_half2(r1, i1);
-                w[1][i] = pack_half2(r2, i2);
-                w[2][i] = pack_half2(r3, i3);
-            }
-            const uint32_t off = kmajor_off16(tid, 8 * q, S::SBO);
-#pragma unroll
-            for (int j = 0; j < 3; ++j)
-                *reinterpret_cast<uint4 *>(sA + j * S::A_BYTES + off) =
-                    make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
+    };
 
-        if (tid == 0) {
+    if (warp == 4) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t j = 0;
+            for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+                const uint32_t s = j % NS, u = j / NS;
+                if (!mbar_wait_or_abort(smem_u32(&empty[s]), (u & 1u) ^ 1u, abort)) break;
+                const uint32_t bar = smem_u32(&full[s]);
+                mbar_arrive_expect_tx(bar, S::TILE_BYTES);
+                float2 *dst = reinterpret_cast<float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
+                const unsigned long long base = tile_base(t);
+                for (uint32_t sg = 0; sg < nseg; ++sg)
+                    bulk_g2s(smem_u32(dst + (size_t)sg * seg_amps), psi + seg_off(base, sg),
+                             seg_bytes, bar);
+            }
+        }
+    } else if (warp == 5) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(S::ROWS, KD);
+            const uint32_t B0 = smem_u32(sB);
+            uint32_t j = 0;
+            for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+                const uint32_t b = j & 1u, u = j >> 1;
+                if (!mbar_wait_or_abort(smem_u32(&a_full[b]), u & 1u, abort)) break;
+                if (!mbar_wait_or_abort(smem_u32(&d_empty[b]), (u & 1u) ^ 1u, abort)) break;
+                tc_fence_after();
+                const uint32_t A0 = smem_u32(smem + S::OFF_A + b * 3u * S::A_BYTES);
+                const uint32_t dset = tmem + b * S::ACC;
+                // (accumulator, A slice, B slice): D0 = A1B1, D1 = A1B2 + A2B1,
+                // D2 = A1B3 + A2B2 + A3B1
+                const uint32_t prod[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0},
+                                             {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
+#pragma unroll
+                for (int p = 0; p < 6; ++p) {
+                    const uint32_t Aa = A0 + prod[p][1] * S::A_BYTES;
+                    const uint32_t Bb = B0 + prod[p][2] * S::B_BYTES;
+                    const bool first_in_acc = (p == 0 || p == 1 || p == 3);
+#pragma unroll
+                    for (uint32_t ks = 0; ks < KD / 16; ++ks)
+                        mma_f16(dset + prod[p][0] * KD, smem_desc(Aa + ks * 256u, 128u, S::SBO),
+                                smem_desc(Bb + ks * 256u, 128u, S::SBO), idesc,
+                                (first_in_acc && ks == 0) ? 0u : 1u);
+                }
+                mma_commit(smem_u32(&a_empty[b]));
+                mma_commit(smem_u32(&d_full[b]));
+            }
+        }
+    } else if (warp < 4) {
+        // ------------------------------------------------------------ transform
+        const uint32_t row = tid;
+        uint32_t coff[D];
+        member_offsets(coff);
+        const uint32_t gbase = group_base(row);
+        uint32_t j = 0;
+        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+            const uint32_t s = j % NS, b = j & 1u;
+            bool ok = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
+            if (!named_bar_and(1, 128, ok)) break;
+            const float2 *rs = reinterpret_cast<const float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
+            float2 v[D];
+            float m = 0.f;
+#pragma unroll
+            for (uint32_t c = 0; c < D; ++c) {
+                v[c] = rs[gbase | coff[c]];
+                m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
+            }
+            fence_proxy_async_smem();             // reads of the raw stage before its refill
+            named_bar(1, 128);
+            if (row == 0) mbar_arrive(smem_u32(&empty[s]));
+            int ex = 0;
+            frexpf(m, &ex);                       // m < 2^ex (m = 0: ex = 0)
+            ex = max(ex, -100);                   // keep 2^(8-ex) finite
+            const float scale = ldexpf(1.f, 8 - ex);   // |x * scale| < 256
+            ok = mbar_wait_or_abort(smem_u32(&a_empty[b]), ((j >> 1) & 1u) ^ 1u, abort);
+            if (!named_bar_and(1, 128, ok)) break;
+            // slot j & 3 was last read by the epilogue of tile j - 4, which finished before
+            // the MMAs of tile j - 2 were issued, whose completion released a_empty[b]
+            row_scale[j & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
+            unsigned char *sA = smem + S::OFF_A + b * 3u * S::A_BYTES;
+#pragma unroll
+            for (uint32_t q = 0; q < D / 4; ++q) {    // 4 amplitudes = 16 bytes per slice
+                uint32_t w[3][4];
+#pragma unroll
+                for (uint32_t i = 0; i < 4; ++i) {
+                    const float2 x = v[4 * q + i];
+                    const float xr = x.x * scale, xi = x.y * scale;
+                    const float r1 = rintf(xr), i1 = rintf(xi);
+                    const float xr2 = (xr - r1) * 512.f, xi2 = (xi - i1) * 512.f;
+                    const float r2 = rintf(xr2), i2 = rintf(xi2);
+                    const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
+                    w[0][i] = pack_half2(r1, i1);
+                    w[1][i] = pack_half2(r2, i2);
+                    w[2][i] = pack_half2(r3, i3);
+                }
+                const uint32_t off = kmajor_off16(row, 8 * q, S::SBO);
+#pragma unroll
+                for (int jj = 0; jj < 3; ++jj)
+                    *reinterpret_cast<uint4 *>(sA + jj * S::A_BYTES + off) =
+                        make_uint4(w[jj][0], w[jj][1], w[jj][2], w[jj][3]);
+            }
+            fence_proxy_async_smem();             // A visible to the tensor cores
+            named_bar(1, 128);
+            if (row == 0) {
+                mbar_arrive(smem_u32(&a_full[b]));
+                mbar_arrive(smem_u32(&scale_full[j & 3u]));
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const uint32_t quad = warp & 3u;          // TMEM lanes 32*quad .. 32*quad+31
+        const uint32_t row = quad * 32u + lane;
+        const uint32_t et = tid - 192u;           // 0..127 within the epilogue warps
+        uint32_t coff[D];
+        member_offsets(coff);
+        const uint32_t gbase = group_base(row);
+        uint32_t j = 0;
+        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+            const uint32_t b = j & 1u, ob = j % NOUT;
+            bool ok = mbar_wait_or_abort(smem_u32(&d_full[b]), (j >> 1) & 1u, abort);
+            ok = ok && mbar_wait_or_abort(smem_u32(&scale_full[j & 3u]), (j >> 2) & 1u, abort);
+            if (!named_bar_and(2, 128, ok)) break;
             tc_fence_after();
-            const uint32_t A0 = smem_u32(sA), B0 = smem_u32(sB);
-            // (accumulator, A slice, B slice) for D0 = A1B1, D1 = A1B2 + A2B1,
-            // D2 = A1B3 + A2B2 + A3B1
-            const uint32_t prod[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
+            if (et == 0) bulk_wait_read<(int)NOUT - 1>();   // this staging tile is free
+            named_bar(2, 128);
+            const float osc = row_scale[j & 3u][row];
+            float2 *out = reinterpret_cast<float2 *>(smem + S::OFF_OUT + ob * S::TILE_BYTES);
+            const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16);
 #pragma unroll
-            for (int p = 0; p < 6; ++p) {
-                const uint32_t acc = prod[p][0];
-                const uint32_t Aa = A0 + prod[p][1] * S::A_BYTES, Bb = B0 + prod[p][2] * S::B_BYTES;
-                const bool first_in_acc = (p == 0 || p == 1 || p == 3);
+            for (uint32_t c0 = 0; c0 < KD; c0 += 32) {
+                float d0[32], d1[32], d2[32];
+                tmem_ld32(lane_addr + c0, d0);
+                tmem_ld32(lane_addr + KD + c0, d1);
+                tmem_ld32(lane_addr + 2 * KD + c0, d2);
 #pragma unroll
-                for (uint32_t ks = 0; ks < KD / 16; ++ks)
-                    mma_f16(tmem + acc * KD, smem_desc(Aa + ks * 256u, 128u, S::SBO),
-                            smem_desc(Bb + ks * 256u, 128u, S::SBO), idesc,
-                            (first_in_acc && ks == 0) ? 0u : 1u);
+                for (uint32_t i = 0; i < 32; i += 2) {
+                    const float re = (d0[i] + (d1[i] + d2[i] * (1.f / 512.f)) * (1.f / 512.f)) * osc;
+                    const float im =
+                        (d0[i + 1] + (d1[i + 1] + d2[i + 1] * (1.f / 512.f)) * (1.f / 512.f)) * osc;
+                    out[gbase | coff[(c0 + i) / 2]] = make_float2(re, im);
+                }
             }
-            mma_commit(smem_u32(&mma_bar));
-            const unsigned long long nt = t + NS * step;   // raw stage s is free again
-            if (nt < a.ntiles) issue_load(nt, s);
-        }
-        const bool ok2 = mbar_wait_bounded(smem_u32(&mma_bar), it & 1u);
-        if (!__syncthreads_and(ok2)) { failed = true; break; }
-        tc_fence_after();
-
-        // row `tid` of D0..D2 -> outputs of this thread's group -> staging tile
-        const uint32_t lane_addr = tmem + ((warp * 32u) << 16);
-#pragma unroll
-        for (uint32_t c0 = 0; c0 < KD; c0 += 32) {
-            float d0[32], d1[32], d2[32];
-            tmem_ld32(lane_addr + c0, d0);
-            tmem_ld32(lane_addr + KD + c0, d1);
-            tmem_ld32(lane_addr + 2 * KD + c0, d2);
-#pragma unroll
-            for (uint32_t i = 0; i < 32; i += 2) {
-                const float re = (d0[i] + (d1[i] + d2[i] * (1.f / 512.f)) * (1.f / 512.f)) * out_scale;
-                const float im = (d0[i + 1] + (d1[i + 1] + d2[i + 1] * (1.f / 512.f)) * (1.f / 512.f)) * out_scale;
-                stage_out[gbase | coff[(c0 + i) / 2]] = make_float2(re, im);
+            tc_fence_before();
+            fence_proxy_async_smem();
+            named_bar(2, 128);
+            if (et == 0) {
+                mbar_arrive(smem_u32(&d_empty[b]));
+                const unsigned long long base = tile_base(t);
+                for (uint32_t sg = 0; sg < nseg; ++sg)
+                    bulk_s2g(psi + seg_off(base, sg), smem_u32(out + (size_t)sg * seg_amps), seg_bytes);
+                bulk_commit();
             }
         }
-        fence_proxy_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned long long base = tile_base(t);
-            for (uint32_t sg = 0; sg < nseg; ++sg)
-                bulk_s2g(psi + seg_off(base, sg), smem_u32(stage_out + (size_t)sg * seg_amps), seg_bytes);
-            bulk_commit();
-        }
+        if (et == 0) bulk_wait_all();
     }
-    if (failed && tid == 0) atomicOr(a.err, 2);
-    if (tid == 0) bulk_wait_all();
+    if (tid == 0 && abort_flag) atomicOr(a.err, 2);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, S::TMEM_COLS);
+    tc_fence_after();
+    if (warp == 5) tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 template <int K>
@@ -304,10 +373,8 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     a.h = p.h;
     for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
     for (int j = 0; j < K; ++j) a.lp[j] = p.lp[j];
-    const int per_sm = (int)std::max<uint32_t>(1u, (227u * 1024u) / (S::SMEM + 2048u));
-    const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles,
-                                                                 (unsigned long long)per_sm * s->num_sms);
-    apply_tc<K><<<grid, 128, S::SMEM, s->stream>>>(a);
+    const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
+    apply_tc<K><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }

@@ -153,6 +153,25 @@ sv_status sv_set_basis(sv_state *s, uint64_t x) {
     return SV_OK;
 }
 
+sv_status sv_set_dtype(sv_state *s, sv_dtype dtype) {
+    clear_error();
+    if (!s) return set_error(SV_ERR_ARG, "sv_set_dtype: null state");
+    if (dtype != SV_C64 && dtype != SV_C128) return set_error(SV_ERR_ARG, "sv_set_dtype: bad dtype");
+    const size_t need = elem_bytes(dtype) << s->n;
+    if (s->cap < need) {
+        if (!s->owned)
+            return set_error(SV_ERR_STATE, "sv_set_dtype: caller buffer too small for this dtype");
+        SV_CUDA(cudaStreamSynchronize(s->stream));
+        SV_CUDA(cudaFree(s->buf));
+        s->buf = nullptr;
+        s->cap = 0;
+        SV_CUDA(cudaMalloc(&s->buf, need));
+        s->cap = need;
+    }
+    s->dtype = dtype;
+    return sv_set_basis(s, 0);
+}
+
 sv_status sv_set_state(sv_state *s, const void *src, int src_on_device) {
     clear_error();
     if (!s || !src) return set_error(SV_ERR_ARG, "sv_set_state: null argument");

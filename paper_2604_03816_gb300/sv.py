@@ -29,7 +29,8 @@ GATE_KINDS = {"i": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "t": 6, "rx": 7, "
               "cnot": 10, "cz": 11, "swap": 12, "toffoli": 13, "u3": 14, "sqrtx": 15,
               "sqrty": 16, "sqrtw": 17, "fsim": 18, "cp": 19, "unitary": 20}
 
-EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "sv_set_state",
+EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "sv_set_dtype",
+           "sv_set_state",
            "sv_get_state", "sv_fuse", "sv_circuit_free", "sv_circuit_size", "sv_circuit_gate",
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
@@ -69,6 +70,7 @@ _sig = {
     "sv_free": [_vp],
     "sv_info": [_vp, ctypes.POINTER(_u32), ctypes.POINTER(_i32), ctypes.POINTER(_vp)],
     "sv_set_basis": [_vp, _u64],
+    "sv_set_dtype": [_vp, _i32],
     "sv_set_state": [_vp, _vp, _i32],
     "sv_get_state": [_vp, _vp, _i32],
     "sv_fuse": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32, ctypes.POINTER(_vp)],
@@ -248,6 +250,10 @@ def sv_info(s: State) -> Tuple[int, int, int]:
 
 def sv_set_basis(s: State, x: int) -> None:
     _check(_lib.sv_set_basis(s.handle, x))
+
+
+def sv_set_dtype(s: State, dtype: int) -> None:
+    _check(_lib.sv_set_dtype(s.handle, dtype))
 
 
 def _np_dtype(dt: int):

@@ -241,6 +241,17 @@ def test_adaptive_promotion_replays_in_c128(gpu):
     psi, rep = run_gpu(sv, n, gl, 0, 3, x=9, adaptive=True)
     assert rep["promotions"] == 1 and rep["dtype_used"] == 1
     check(psi, ref, 1)
+    # back to complex64 on the same state object
+    c = sv.sv_fuse(sv.gates_from_specs(specs), n, 3)
+    s = sv.sv_alloc(n, 0)
+    sv.sv_apply_circuit(s, sv.sv_fuse(gl, n, 3), adaptive=True)
+    assert sv.sv_info(s)[1] == 1
+    sv.sv_set_dtype(s, 0)
+    assert sv.sv_info(s)[1] == 0 and sv.sv_topk(s, 1)[0][0] == 0
+    sv.sv_set_basis(s, 9)
+    sv.sv_apply_circuit(s, c)
+    check(sv.sv_get_state(s).astype(np.complex128), oracle.simulate(n, specs, x=9), 0)
+    s.free()
     # unitary circuit: no promotion, stays complex64
     psi2, rep2 = run_gpu(sv, n, sv.gates_from_specs(specs), 0, 3, x=9, adaptive=True)
     assert rep2["promotions"] == 0 and rep2["dtype_used"] == 0 and rep2["drift"] < 1e-6
