@@ -56,6 +56,13 @@ def parse():
     ap.add_argument("--compare-unfused", action="store_true",
                     help="also time the unfused complex128 per-gate form once")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+                    help="single: the 30-qubit hot path (default line); batched: 512 HEA "
+                         "circuits of 16-22 qubits; serve: Poisson request stream")
+    ap.add_argument("--count", type=int, default=512, help="batched: number of circuits")
+    ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serve: req/s list")
+    ap.add_argument("--duration", type=float, default=4.0, help="serve: seconds per rate")
+    ap.add_argument("--max-requests", type=int, default=40, help="serve: requests per rate")
     return ap.parse_args()
 
 
@@ -201,6 +208,54 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args):
+    """Poisson arrivals (each rate in --rates) of seeded brickwork circuits, width
+    U{10..30}, depth U{10..60}, 70% complex64 / 30% complex128, top-64 outcomes, under a
+    150 GiB HBM budget; at most --max-requests per rate.  Latency = server clock from
+    submission to the result being ready."""
+    import torch
+    from paper_2604_03816_gb300 import sv
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    per_rate = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        reqs = W.serving_stream(rate, args.duration)[: args.max_requests]
+        arrays = [sv.GateArray(sv.gates_from_specs(r.gates)) for r in reqs]
+        srv = sv.sv_server_create(budget_bytes=150 << 30, max_slots=16, max_k=4)
+        t0 = time.perf_counter()
+        ids = {}
+        got = {}
+        for r, ga in zip(reqs, arrays):
+            while time.perf_counter() - t0 < r.arrival_s:
+                for x in sv.sv_server_poll(srv, 256, 0):
+                    got[x["id"]] = x
+                time.sleep(0.0002)
+            ids[sv.sv_server_submit(srv, r.width, 0 if r.dtype == "c64" else 1, ga)] = r
+        while len(got) < len(ids):
+            for x in sv.sv_server_poll(srv, 256, 20):
+                got[x["id"]] = x
+        srv.destroy()
+        lat = np.array([got[i]["t_done"] - got[i]["t_submit"] for i in ids])
+        first = min(got[i]["t_submit"] for i in ids)
+        last = max(got[i]["t_done"] for i in ids)
+        ok = sum(1 for i in ids if got[i]["status"] == 0)
+        per_rate.append({"rate_hz": rate, "requests": len(ids), "ok": ok,
+                         "p50_ms": 1000 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                         "circuits_per_s": len(ids) / (last - first),
+                         "c128_share": sum(1 for r in reqs if r.dtype == "c128") / len(reqs)})
+    best = max(per_rate, key=lambda d: d["circuits_per_s"])
+    out = {"metric": "served circuits/s with p50/p99 latency (Poisson arrivals, 10-30 qubits, "
+                     "70% c64 / 30% c128, top-64)",
+           "value": best["circuits_per_s"], "unit": "circuits/s", "n_gpus": world,
+           "steps": len(per_rate), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "mixed f32/f64", "data": "synthetic",
+           "config": {"workload": "serving_stream", "budget_gib": 150, "max_slots": 16,
+                      "max_k": 4, "max_requests_per_rate": args.max_requests},
+           "per_rate": per_rate}
+    print(json.dumps(out), flush=True)
+
+
 def config_dict(args, ngates, nfused):
     return {"workload": f"grid_random {args.n}q depth {args.cycles} "
                         f"({'sqrtX/sqrtY/sqrtW + fSim(pi/2,pi/6)'}), {args.dtype}, "
@@ -211,10 +266,98 @@ def config_dict(args, ngates, nfused):
             "seed": W.seed_for(3, args.n)}
 
 
+def run_batched(args):
+    """512 hardware-efficient-ansatz circuits (widths U{16,18,20,22}, 6 layers of
+    RY RZ + CNOT ladder, complex64), <sum Z_i Z_{i+1}> per circuit.  Per width: one batch,
+    fusion width and chunking from the autotuner (tuned once, before timing).  One step =
+    fusion of every circuit (sv_fuse for one, sv_fuse_like for the rest) + sv_batch_apply
+    per width (CUDA-graph replay) + sv_batch_expect per width."""
+    import torch
+    from paper_2604_03816_gb300 import sv
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    fam = W.hea_batch(args.count)
+    widths = sorted({w for w, _ in fam})
+    groups = {w: [g for ww, g in fam if ww == w] for w in widths}
+    gates = {w: [sv.gates_from_specs(g) for g in groups[w]] for w in widths}
+    arrays = {w: [sv.GateArray(g) for g in gates[w]] for w in widths}   # the input circuits
+    batches, tune = {}, {}
+    with torch.cuda.stream(stream):
+        for w in widths:
+            batches[w] = sv.sv_batch_alloc(w, sv.SV_C64, len(groups[w]), stream=stream)
+            tune[w] = sv.sv_batch_tune(batches[w], gates[w][0], 1, 4)
+
+        def step():
+            fuse_s = 0.0
+            out = {}
+            for w in widths:
+                t0 = time.perf_counter()
+                # Algorithm 2 once per width; the other circuits of the family replay its
+                # decisions (same qubits, other angles)
+                pattern = sv.sv_fuse(arrays[w][0], w, tune[w]["best_k"])
+                circs = [pattern] + [sv.sv_fuse_like(pattern, ga) for ga in arrays[w][1:]]
+                fuse_s += time.perf_counter() - t0
+                sv.sv_batch_set_basis(batches[w], 0)
+                sv.sv_batch_apply(batches[w], circs, l2_bytes=tune[w]["l2_bytes"])
+                xs, zs, cs = W.zz_chain(w)
+                out[w] = sv.sv_batch_expect(batches[w], xs, zs, cs)
+            return fuse_s, out
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fuse_total = 0.0
+        for _ in range(args.steps):
+            fs, out = step()
+            fuse_total += fs
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        # the same circuits one by one through sv_apply_circuit (unbatched), for context
+        s1 = sv.sv_alloc(max(widths), sv.SV_C64, stream=stream)
+        sample = [(w, gates[w][i]) for w in widths for i in range(4)]
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        states = {w: sv.sv_alloc(w, sv.SV_C64, stream=stream) for w in widths}
+        f0.record(stream)
+        for w, g in sample:
+            c = sv.sv_fuse(g, w, tune[w]["best_k"])
+            sv.sv_set_basis(states[w], 0)
+            sv.sv_apply_circuit(states[w], c)
+            xs, zs, cs = W.zz_chain(w)
+            sv.sv_expect(states[w], xs, zs, cs)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        unb = len(sample) / (f0.elapsed_time(f1) / 1000.0)
+        s1.free()
+    value = args.count * args.steps / (ms / 1000.0)
+    out = {"metric": "batched circuits/s (HEA, 16-22 qubits, complex64, <sum ZZ> per circuit)",
+           "value": value, "unit": "circuits/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{args.count} hea circuits, widths {widths}, 6 layers, c64",
+                      "per_width": {str(w): {"circuits": len(groups[w]),
+                                             "best_k": tune[w]["best_k"],
+                                             "l2_chunk_bytes": tune[w]["l2_bytes"],
+                                             "tune_ms": tune[w]["ms"]} for w in widths}},
+           "host_fusion_s_per_step": fuse_total / args.steps,
+           "unbatched_circuits_per_s": unb,
+           "speedup_vs_unbatched": value / unb}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "batched":
+        run_batched(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
     rank, world, local = dist_info()
     import torch

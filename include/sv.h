@@ -127,6 +127,13 @@ sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device);
  * Copies the matrices; free the result with sv_circuit_free.  Host only. */
 sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k,
                   sv_circuit **out);
+/* Fuse `gates` with the decisions sv_fuse made for `pattern` (the gates must act on the
+ * same qubits, gate by gate, as the ones `pattern` was fused from; matrices may differ --
+ * a parameter sweep).  Algorithm 2's decisions depend only on the qubit sets, so the
+ * result equals sv_fuse(gates, n, max_k) bit for bit, without repeating the DAG search.
+ * SV_ERR_ARG if the qubits differ.  Host only. */
+sv_status sv_fuse_like(const sv_circuit *pattern, const sv_gate *gates, size_t ngates,
+                       sv_circuit **out);
 sv_status sv_circuit_free(sv_circuit *c);
 /* Number of fused gates and the qubit count the circuit was built for. */
 sv_status sv_circuit_size(const sv_circuit *c, size_t *nfused, uint32_t *n);
@@ -195,6 +202,118 @@ sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
  * the CUDA cores). */
 #define SV_POLICY_NO_TENSOR_CORES 1u   /* always use the CUDA-core kernels */
 sv_status sv_set_policy(sv_state *s, uint32_t flags);
+
+/* ------------------------------------------------------------ batched execution */
+
+/* A batch: `count` states of n qubits in one dtype, stored back to back (state i at
+ * amplitude offset i * 2^n), each driven by its own circuit.  All circuits applied in one
+ * call must share their fused structure (same number of fused gates, same targets gate
+ * by gate) -- one parameterised circuit family fused with one width; the matrices may
+ * differ.  The library keeps a device table of the per-state matrices, processes the
+ * states in L2-sized chunks (all gates of a chunk before the next chunk) and captures
+ * the launch sequence in a CUDA graph, replayed while the structure and chunking stay
+ * the same.  Work is enqueued on the batch's stream. */
+typedef struct sv_batch sv_batch;
+
+typedef struct {
+    uint32_t chunk_states;   /* states per chunk (0: as many as fit l2_bytes) */
+    size_t l2_bytes;         /* chunk budget in bytes (0: 64 MiB) */
+    uint32_t no_graph;       /* 1: launch directly instead of through the CUDA graph */
+    uint32_t timing;         /* 1: time the passes with CUDA events (synchronises) */
+} sv_batch_opts;
+
+typedef struct {
+    uint64_t passes;         /* fused gates x states */
+    uint64_t launches;       /* kernel launches (fused gates x chunks) */
+    uint64_t bytes;          /* algorithmic bytes: passes * 2 * 2^n * s */
+    uint32_t chunk_states;
+    uint32_t graph_reused;   /* 1 if a previously captured graph was replayed */
+    double apply_ms;         /* with opts->timing */
+} sv_batch_report;
+
+typedef struct {
+    uint32_t best_k;         /* fusion width with the shortest batched apply */
+    size_t l2_bytes;         /* chunk budget that achieved it */
+    double best_ms;
+    double ms[SV_MAX_K + 1]; /* best time per width (index k), 0 if not tried */
+    uint32_t cached;         /* 1 if the answer came from the cache */
+} sv_tune_result;
+
+/* count in 1..65535; dev_buf: caller buffer of >= count * 2^n * s bytes or NULL.  All
+ * states start as |0...0>. */
+sv_status sv_batch_alloc(uint32_t n, sv_dtype dtype, uint32_t count, void *dev_buf, size_t bytes,
+                         void *stream, sv_batch **out);
+sv_status sv_batch_free(sv_batch *b);
+sv_status sv_batch_set_basis(sv_batch *b, uint64_t x);     /* every state to |x>; async */
+/* Copy state i (2^n amplitudes) to host (synchronises) or device memory. */
+sv_status sv_batch_get_state(sv_batch *b, uint32_t i, void *dst, int dst_on_device);
+/* Apply circuits[i] to state i for all i < count (see above).  opts and rep may be NULL.
+ * SV_ERR_ARG if a circuit does not share the structure of circuits[0]. */
+sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const sv_batch_opts *opts,
+                         sv_batch_report *rep);
+/* out[i] = sum_t coef[t] <psi_i| P_t |psi_i> for every state (host array of count
+ * doubles), FP64 accumulation.  Synchronises. */
+sv_status sv_batch_expect(sv_batch *b, const uint64_t *xmask, const uint64_t *zmask,
+                          const double *coef, size_t nterms, double *out);
+sv_status sv_batch_sync(sv_batch *b);
+/* Autotuner: fuse `gates` (one representative circuit of the family) at every width
+ * kmin..kmax, time the batched apply on this batch for three chunk budgets (32, 64,
+ * 96 MiB), and return the fastest; results are cached per batch shape and target
+ * sequence (the measure-once-and-cache idea of Algorithm 1, applied to the fusion width
+ * and the chunking).  Overwrites the batch's states with |0...0>.  Synchronises. */
+sv_status sv_batch_tune(sv_batch *b, const sv_gate *gates, size_t ngates, uint32_t kmin, uint32_t kmax,
+                        sv_tune_result *out);
+
+/* ------------------------------------------------------------------ serving */
+
+/* A continuous-batching request server on the current device.  Submitted circuits are
+ * fused on host threads (Algorithm 2), then admitted in arrival order while their memory
+ * (Eq. 14: 2^n s + (2^k)^2 s + workspace) fits the budget and a slot is free -- requests
+ * that do not fit wait in the queue (no CPU fallback).  Each slot is a CUDA stream; the
+ * request's state is allocated from the stream-ordered pool, set to |0...0>, every fused
+ * pass is applied and the top-k outcomes are returned.  Requests in different slots
+ * overlap on the GPU; each result is computed by the same kernels in the same order as
+ * alone, so it does not depend on the other requests in flight. */
+typedef struct sv_server sv_server;
+
+typedef struct {
+    size_t budget_bytes;     /* HBM budget of admitted requests (0: 150 GiB) */
+    uint32_t max_slots;      /* requests in flight on the GPU (0: 16; at most 256) */
+    uint32_t topk;           /* outcomes per result, 1..64 (0: 64) */
+    uint32_t max_k;          /* fusion width 1..5 (0: 4) */
+    uint32_t fuse_threads;   /* host threads that fuse submitted circuits (0: 4) */
+} sv_server_config;
+
+typedef struct {
+    uint64_t id;             /* as returned by sv_server_submit */
+    int32_t status;          /* sv_status of this request */
+    int32_t dtype_used;
+    uint32_t n;
+    uint32_t k;              /* outcomes in idx / p: min(topk, 2^n) */
+    uint64_t passes;         /* fused gates applied */
+    uint64_t idx[64];        /* most probable outcomes, probability descending, ties to */
+    double p[64];            /* the lower index */
+    double t_submit, t_admit, t_done;   /* seconds on the server's clock */
+} sv_server_result;
+
+typedef struct {
+    uint64_t submitted, completed, queued;
+    uint32_t active;
+    size_t in_use_bytes, budget_bytes;
+    double now;              /* the server's clock (seconds since creation) */
+} sv_server_stats;
+
+sv_status sv_server_create(const sv_server_config *cfg, sv_server **out);   /* cfg may be NULL */
+/* Queue a circuit (gates as for sv_fuse; copied) for an n-qubit state in dtype.  Returns
+ * at once with the request id; the latency clock starts here. */
+sv_status sv_server_submit(sv_server *s, uint32_t n, sv_dtype dtype, const sv_gate *gates,
+                           size_t ngates, uint64_t *id);
+/* Move up to cap finished results into out (*nout of them); waits up to wait_ms for the
+ * first one when none is ready. */
+sv_status sv_server_poll(sv_server *s, sv_server_result *out, size_t cap, size_t *nout, int wait_ms);
+sv_status sv_server_get_stats(sv_server *s, sv_server_stats *out);
+/* Finish every queued and running request, then release everything. */
+sv_status sv_server_destroy(sv_server *s);
 
 /* sum_t coef[t] <psi| P_t |psi> (as sv_expect) for a caller-owned device state, written
  * to out_dev (one double in device memory), enqueued on `stream` (NULL = the legacy

@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(256) apply_tile(const __grid_constant__ ApplyA
             if ((c >> j) & 1) o |= 1u << a.lp[j];
         coff[c] = o;
     }
+    SegLanes sl;
+    sl.init(a.L, a.h, a.hi, threadIdx.x & 31u);
     if (threadIdx.x == 0) {
         mbar_init(barp, 1);
         fence_mbar_init();
@@ -77,23 +79,18 @@ __global__ void __launch_bounds__(256) apply_tile(const __grid_constant__ ApplyA
 
     uint32_t parity = 0;
     for (unsigned long long t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-        unsigned long long base = t << a.L;
-        for (uint32_t j = 0; j < a.h; ++j) base = insert_zero64(base, a.hi[j]);
-        if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(barp, seg_bytes * nseg);
-            for (uint32_t s = 0; s < nseg; ++s) {
-                unsigned long long off = base;
-                for (uint32_t j = 0; j < a.h; ++j)
-                    if ((s >> j) & 1u) off |= 1ull << a.hi[j];
-                bulk_g2s(smem_u32(tile + (size_t)s * seg_amps), psi + off, seg_bytes, barp);
-            }
+        const unsigned long long base = sl.base(t);
+        if (threadIdx.x < 32) {                 // warp 0: lane i copies segment i
+            if (threadIdx.x == 0) mbar_arrive_expect_tx(barp, seg_bytes * nseg);
+            __syncwarp();
+            if (threadIdx.x < nseg)
+                bulk_g2s(smem_u32(tile + (size_t)threadIdx.x * seg_amps), psi + base + sl.my_off,
+                         seg_bytes, barp);
         }
         const bool ok = mbar_wait_bounded(barp, parity);
         if (!__syncthreads_and(ok)) {
-            if (threadIdx.x == 0) {
-                atomicOr(a.err, 1);
-                bulk_wait_all();
-            }
+            if (threadIdx.x == 0) atomicOr(a.err, 1);
+            if (threadIdx.x < 32) bulk_wait_all();
             return;
         }
         parity ^= 1u;
@@ -121,19 +118,15 @@ __global__ void __launch_bounds__(256) apply_tile(const __grid_constant__ ApplyA
         }
         fence_proxy_async_smem();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            for (uint32_t s = 0; s < nseg; ++s) {
-                unsigned long long off = base;
-                for (uint32_t j = 0; j < a.h; ++j)
-                    if ((s >> j) & 1u) off |= 1ull << a.hi[j];
-                bulk_s2g(psi + off, smem_u32(tile + (size_t)s * seg_amps), seg_bytes);
-            }
+        if (threadIdx.x < 32) {
+            if (threadIdx.x < nseg)
+                bulk_s2g(psi + base + sl.my_off, smem_u32(tile + (size_t)threadIdx.x * seg_amps), seg_bytes);
             bulk_commit();
             bulk_wait_read_all();
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) bulk_wait_all();
+    if (threadIdx.x < 32) bulk_wait_all();
 }
 
 // Tile bits per (precision, k): 32 KB tiles for k <= 3, larger tiles for k = 4, 5 so

@@ -24,14 +24,17 @@
 //   warp 4 (one thread)  TMA producer: 1-D bulk loads of each tile's 2^h segments into a
 //                        ring of NS raw stages;
 //   warps 0-3            transform: one group (row of A) per thread -- gather from the
-//                        raw stage, cut into three 9-bit slices, 16-byte stores into the
-//                        K-major canonical layout of A (double-buffered);
-//   warp 5 (one thread)  MMA issuer: 6 x K/16 tcgen05.mma.kind::f16 into three TMEM
-//                        accumulators (double-buffered), committed to mbarriers;
+//                        raw stage, cut into three 9-bit slices and write them into
+//                        tensor memory with tcgen05.st (the thread's own TMEM lane);
+//   warp 5 (one thread)  MMA issuer: 6 x K/16 tcgen05.mma.kind::f16, A from TMEM and B
+//                        from shared memory, into three TMEM accumulators
+//                        (double-buffered), committed to mbarriers;
 //   warps 6-9            epilogue: tcgen05.ld of their 32-lane quadrant, combine, scatter
 //                        into an output staging tile, TMA bulk stores.
-// So loads, slicing, MMAs and stores of consecutive tiles overlap.  Every wait is
-// bounded and any role that gives up makes the others leave too (abort flag).
+// So loads, slicing, MMAs and stores of consecutive tiles overlap.  With A in tensor
+// memory, shared memory holds only B, the raw stages and the output staging, so 4 (k = 5)
+// or 8 (k = 4) tiles of loads can be in flight per SM.  Every wait is bounded and any
+// role that gives up makes the others leave too (abort flag).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -54,15 +57,16 @@ struct TcShape {
     static constexpr uint32_t ROWS = 128;             // groups per tile (MMA M)
     static constexpr uint32_t TB = K + 7;             // tile bits
     static constexpr uint32_t TILE_BYTES = ROWS * D * 8u;
-    static constexpr uint32_t A_BYTES = ROWS * KD * 2u;   // one FP16 slice of A
     static constexpr uint32_t B_BYTES = KD * KD * 2u;     // one FP16 slice of B
-    static constexpr uint32_t SBO = (KD / 8u) * 128u;     // 8-row group stride
-    static constexpr uint32_t NS = K == 5 ? 2u : 4u;      // raw stages
-    static constexpr uint32_t NOUT = K == 5 ? 1u : 2u;    // output staging buffers
+    static constexpr uint32_t SBO = (KD / 8u) * 128u;     // 8-row group stride of B
+    static constexpr uint32_t NS = K == 5 ? 4u : 8u;      // raw stages
+    static constexpr uint32_t NOUT = 2u;                  // output staging tiles
     static constexpr uint32_t ACC = 3u * KD;              // TMEM columns of one D set
-    static constexpr uint32_t TMEM_COLS = K == 5 ? 512u : 256u;   // two D sets
-    static constexpr uint32_t OFF_A = 3u * B_BYTES;
-    static constexpr uint32_t OFF_RAW = OFF_A + 2u * 3u * A_BYTES;
+    static constexpr uint32_t A_COLS = KD / 2u;           // TMEM columns of one A slice
+    static constexpr uint32_t A_COL0 = 2u * ACC;          // first column of A
+    static constexpr uint32_t TMEM_COLS = K == 5 ? 512u : 256u;
+    static_assert(A_COL0 + 3u * A_COLS <= TMEM_COLS, "TMEM layout");
+    static constexpr uint32_t OFF_RAW = 3u * B_BYTES;
     static constexpr uint32_t OFF_OUT = OFF_RAW + NS * TILE_BYTES;
     static constexpr uint32_t SMEM = OFF_OUT + NOUT * TILE_BYTES;
     static constexpr uint32_t THREADS = 320;              // 10 warps
@@ -91,13 +95,13 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
     constexpr uint32_t D = S::D, KD = S::KD, NS = S::NS, NOUT = S::NOUT;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
-    __shared__ __align__(8) unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2];
+    __shared__ __align__(8) unsigned long long a_full, a_empty, d_full[2], d_empty[2];
     __shared__ __align__(8) unsigned long long scale_full[4];   // row scales, tile j -> j & 3
     __shared__ float row_scale[4][128];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
-    // B slices, then two sets of A slices, the raw stages and the output staging tiles;
-    // operand reads stay inside the CTA's shared memory whatever the descriptor strides.
+    // B slices, the raw stages and the output staging tiles; B operand reads stay inside
+    // the CTA's shared memory whatever the descriptor strides.
     unsigned char *sB = smem;
     float2 *psi = reinterpret_cast<float2 *>(a.psi);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -115,9 +119,9 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
+        mbar_init(smem_u32(&a_full), 1);
+        mbar_init(smem_u32(&a_empty), 1);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&a_full[b]), 1);
-            mbar_init(smem_u32(&a_empty[b]), 1);
             mbar_init(smem_u32(&d_full[b]), 1);
             mbar_init(smem_u32(&d_empty[b]), 1);
         }
@@ -139,17 +143,6 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
     volatile int *abort = &abort_flag;
     const unsigned long long first = blockIdx.x, step = gridDim.x;
 
-    auto tile_base = [&](unsigned long long t) {
-        unsigned long long base = t << a.L;
-        for (uint32_t j = 0; j < a.h; ++j) base = insert_zero64(base, a.hi[j]);
-        return base;
-    };
-    auto seg_off = [&](unsigned long long base, uint32_t sg) {
-        unsigned long long off = base;
-        for (uint32_t j = 0; j < a.h; ++j)
-            if ((sg >> j) & 1u) off |= 1ull << a.hi[j];
-        return off;
-    };
     auto group_base = [&](uint32_t row) {
         uint32_t g = row;
 #pragma unroll
@@ -169,18 +162,22 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
 
     if (warp == 4) {
         // ------------------------------------------------------------ TMA producer
-        if (lane == 0) {
-            uint32_t j = 0;
-            for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
-                const uint32_t s = j % NS, u = j / NS;
-                if (!mbar_wait_or_abort(smem_u32(&empty[s]), (u & 1u) ^ 1u, abort)) break;
-                const uint32_t bar = smem_u32(&full[s]);
-                mbar_arrive_expect_tx(bar, S::TILE_BYTES);
+        // lane i issues the bulk copy of segment i of every tile
+        SegLanes sl;
+        sl.init(a.L, a.h, a.hi, lane);
+        uint32_t j = 0;
+        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+            const uint32_t s = j % NS, u = j / NS;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait_or_abort(smem_u32(&empty[s]), (u & 1u) ^ 1u, abort);
+            if (!__shfl_sync(0xffffffffu, (int)ok, 0)) break;
+            const uint32_t bar = smem_u32(&full[s]);
+            if (lane == 0) mbar_arrive_expect_tx(bar, S::TILE_BYTES);
+            __syncwarp();
+            if (lane < nseg) {
                 float2 *dst = reinterpret_cast<float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
-                const unsigned long long base = tile_base(t);
-                for (uint32_t sg = 0; sg < nseg; ++sg)
-                    bulk_g2s(smem_u32(dst + (size_t)sg * seg_amps), psi + seg_off(base, sg),
-                             seg_bytes, bar);
+                bulk_g2s(smem_u32(dst + (size_t)lane * seg_amps), psi + sl.base(t) + sl.my_off,
+                         seg_bytes, bar);
             }
         }
     } else if (warp == 5) {
@@ -191,10 +188,10 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             uint32_t j = 0;
             for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
                 const uint32_t b = j & 1u, u = j >> 1;
-                if (!mbar_wait_or_abort(smem_u32(&a_full[b]), u & 1u, abort)) break;
+                if (!mbar_wait_or_abort(smem_u32(&a_full), j & 1u, abort)) break;
                 if (!mbar_wait_or_abort(smem_u32(&d_empty[b]), (u & 1u) ^ 1u, abort)) break;
                 tc_fence_after();
-                const uint32_t A0 = smem_u32(smem + S::OFF_A + b * 3u * S::A_BYTES);
+                const uint32_t A0 = tmem + S::A_COL0;
                 const uint32_t dset = tmem + b * S::ACC;
                 // (accumulator, A slice, B slice): D0 = A1B1, D1 = A1B2 + A2B1,
                 // D2 = A1B3 + A2B2 + A3B1
@@ -202,16 +199,16 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
                                              {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
 #pragma unroll
                 for (int p = 0; p < 6; ++p) {
-                    const uint32_t Aa = A0 + prod[p][1] * S::A_BYTES;
+                    const uint32_t Aa = A0 + prod[p][1] * S::A_COLS;
                     const uint32_t Bb = B0 + prod[p][2] * S::B_BYTES;
                     const bool first_in_acc = (p == 0 || p == 1 || p == 3);
 #pragma unroll
                     for (uint32_t ks = 0; ks < KD / 16; ++ks)
-                        mma_f16(dset + prod[p][0] * KD, smem_desc(Aa + ks * 256u, 128u, S::SBO),
-                                smem_desc(Bb + ks * 256u, 128u, S::SBO), idesc,
-                                (first_in_acc && ks == 0) ? 0u : 1u);
+                        mma_f16_tmem_a(dset + prod[p][0] * KD, Aa + ks * 8u,
+                                       smem_desc(Bb + ks * 256u, 128u, S::SBO), idesc,
+                                       (first_in_acc && ks == 0) ? 0u : 1u);
                 }
-                mma_commit(smem_u32(&a_empty[b]));
+                mma_commit(smem_u32(&a_empty));
                 mma_commit(smem_u32(&d_full[b]));
             }
         }
@@ -223,7 +220,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
         const uint32_t gbase = group_base(row);
         uint32_t j = 0;
         for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
-            const uint32_t s = j % NS, b = j & 1u;
+            const uint32_t s = j % NS;
             bool ok = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
             if (!named_bar_and(1, 128, ok)) break;
             const float2 *rs = reinterpret_cast<const float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
@@ -241,37 +238,39 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             frexpf(m, &ex);                       // m < 2^ex (m = 0: ex = 0)
             ex = max(ex, -100);                   // keep 2^(8-ex) finite
             const float scale = ldexpf(1.f, 8 - ex);   // |x * scale| < 256
-            ok = mbar_wait_or_abort(smem_u32(&a_empty[b]), ((j >> 1) & 1u) ^ 1u, abort);
+            ok = mbar_wait_or_abort(smem_u32(&a_empty), (j & 1u) ^ 1u, abort);
             if (!named_bar_and(1, 128, ok)) break;
+            tc_fence_after();
             // slot j & 3 was last read by the epilogue of tile j - 4, which finished before
-            // the MMAs of tile j - 2 were issued, whose completion released a_empty[b]
+            // the MMAs of tile j - 1 were issued, whose completion released a_empty
             row_scale[j & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
-            unsigned char *sA = smem + S::OFF_A + b * 3u * S::A_BYTES;
+            // three 9-bit integer slices, one FP16 pair (re, im) per 32-bit TMEM column
+            uint32_t w1[D], w2[D], w3[D];
 #pragma unroll
-            for (uint32_t q = 0; q < D / 4; ++q) {    // 4 amplitudes = 16 bytes per slice
-                uint32_t w[3][4];
-#pragma unroll
-                for (uint32_t i = 0; i < 4; ++i) {
-                    const float2 x = v[4 * q + i];
-                    const float xr = x.x * scale, xi = x.y * scale;
-                    const float r1 = rintf(xr), i1 = rintf(xi);
-                    const float xr2 = (xr - r1) * 512.f, xi2 = (xi - i1) * 512.f;
-                    const float r2 = rintf(xr2), i2 = rintf(xi2);
-                    const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
-                    w[0][i] = pack_half2(r1, i1);
-                    w[1][i] = pack_half2(r2, i2);
-                    w[2][i] = pack_half2(r3, i3);
-                }
-                const uint32_t off = kmajor_off16(row, 8 * q, S::SBO);
-#pragma unroll
-                for (int jj = 0; jj < 3; ++jj)
-                    *reinterpret_cast<uint4 *>(sA + jj * S::A_BYTES + off) =
-                        make_uint4(w[jj][0], w[jj][1], w[jj][2], w[jj][3]);
+            for (uint32_t c = 0; c < D; ++c) {
+                const float xr = v[c].x * scale, xi = v[c].y * scale;
+                const float r1 = rintf(xr), i1 = rintf(xi);
+                const float xr2 = (xr - r1) * 512.f, xi2 = (xi - i1) * 512.f;
+                const float r2 = rintf(xr2), i2 = rintf(xi2);
+                const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
+                w1[c] = pack_half2(r1, i1);
+                w2[c] = pack_half2(r2, i2);
+                w3[c] = pack_half2(r3, i3);
             }
-            fence_proxy_async_smem();             // A visible to the tensor cores
+            const uint32_t arow = tmem + S::A_COL0 + ((warp * 32u) << 16);
+            if constexpr (D == 32) {
+                tmem_st32(arow, w1);
+                tmem_st32(arow + S::A_COLS, w2);
+                tmem_st32(arow + 2 * S::A_COLS, w3);
+            } else {
+                tmem_st16(arow, w1);
+                tmem_st16(arow + S::A_COLS, w2);
+                tmem_st16(arow + 2 * S::A_COLS, w3);
+            }
+            tc_fence_before();
             named_bar(1, 128);
             if (row == 0) {
-                mbar_arrive(smem_u32(&a_full[b]));
+                mbar_arrive(smem_u32(&a_full));
                 mbar_arrive(smem_u32(&scale_full[j & 3u]));
             }
         }
@@ -283,6 +282,8 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
         uint32_t coff[D];
         member_offsets(coff);
         const uint32_t gbase = group_base(row);
+        SegLanes sl;                              // the first epilogue warp stores segments
+        sl.init(a.L, a.h, a.hi, lane);
         uint32_t j = 0;
         for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
             const uint32_t b = j & 1u, ob = j % NOUT;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             ok = ok && mbar_wait_or_abort(smem_u32(&scale_full[j & 3u]), (j >> 2) & 1u, abort);
             if (!named_bar_and(2, 128, ok)) break;
             tc_fence_after();
-            if (et == 0) bulk_wait_read<(int)NOUT - 1>();   // this staging tile is free
+            if (et < 32) bulk_wait_read<(int)NOUT - 1>();   // this staging tile is free
             named_bar(2, 128);
             const float osc = row_scale[j & 3u][row];
             float2 *out = reinterpret_cast<float2 *>(smem + S::OFF_OUT + ob * S::TILE_BYTES);
@@ -312,15 +313,15 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             tc_fence_before();
             fence_proxy_async_smem();
             named_bar(2, 128);
-            if (et == 0) {
-                mbar_arrive(smem_u32(&d_empty[b]));
-                const unsigned long long base = tile_base(t);
-                for (uint32_t sg = 0; sg < nseg; ++sg)
-                    bulk_s2g(psi + seg_off(base, sg), smem_u32(out + (size_t)sg * seg_amps), seg_bytes);
+            if (et == 0) mbar_arrive(smem_u32(&d_empty[b]));
+            if (et < 32) {
+                if (lane < nseg)
+                    bulk_s2g(psi + sl.base(t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
+                             seg_bytes);
                 bulk_commit();
             }
         }
-        if (et == 0) bulk_wait_all();
+        if (et < 32) bulk_wait_all();
     }
     if (tid == 0 && abort_flag) atomicOr(a.err, 2);
     tc_fence_before();

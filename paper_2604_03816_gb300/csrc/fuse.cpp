@@ -53,6 +53,23 @@ std::vector<cplx> embed(const Gate &g, const uint32_t *qs, uint32_t m) {
     return e;
 }
 
+// Eq. 9: U_fused = U_v . U_u on the sorted qubit set qs (size m), u applied first.
+Gate fused_product(const Gate &gu, const Gate &gv, const uint32_t *qs, uint32_t m) {
+    const std::vector<cplx> eu = embed(gu, qs, m), ev = embed(gv, qs, m);
+    const int d = 1 << m;
+    Gate f;
+    f.k = m;
+    for (uint32_t j = 0; j < m; ++j) f.t[j] = qs[j];
+    f.u.assign((size_t)d * d, cplx(0.0, 0.0));
+    for (int r = 0; r < d; ++r)
+        for (int x = 0; x < d; ++x) {
+            const cplx a = ev[(size_t)r * d + x];
+            if (a == cplx(0.0, 0.0)) continue;
+            for (int c = 0; c < d; ++c) f.u[(size_t)r * d + c] += a * eu[(size_t)x * d + c];
+        }
+    return f;
+}
+
 class Dag {
   public:
     Dag(const std::vector<Gate> &gates, uint32_t n) : nodes_(gates.size()), seen_(gates.size(), 0) {
@@ -120,19 +137,7 @@ class Dag {
 
     void contract(int u, int v, const uint32_t *qs, uint32_t m) {
         Node &U = nodes_[u], &V = nodes_[v];
-        const std::vector<cplx> eu = embed(U.g, qs, m), ev = embed(V.g, qs, m);
-        const int d = 1 << m;
-        Gate f;
-        f.k = m;
-        for (uint32_t j = 0; j < m; ++j) f.t[j] = qs[j];
-        f.u.assign((size_t)d * d, cplx(0.0, 0.0));
-        for (int r = 0; r < d; ++r)            // Eq. 9: U_fused = U_v . U_u
-            for (int x = 0; x < d; ++x) {
-                const cplx a = ev[(size_t)r * d + x];
-                if (a == cplx(0.0, 0.0)) continue;
-                for (int c = 0; c < d; ++c) f.u[(size_t)r * d + c] += a * eu[(size_t)x * d + c];
-            }
-        U.g = std::move(f);
+        U.g = fused_product(U.g, V.g, qs, m);
         for (int w : V.preds)
             if (w != u) {
                 nodes_[w].succs.erase(v);
@@ -158,8 +163,9 @@ class Dag {
 
 }  // namespace
 
-std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k) {
+std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k, FusePlan *plan) {
     Dag dag(in, n);
+    if (plan) plan->contractions.clear();
     bool changed = max_k > 0;
     while (changed) {
         changed = false;
@@ -172,13 +178,33 @@ std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t m
                 if (m > max_k) continue;
                 if (dag.other_path(u, v)) continue;
                 dag.contract(u, v, qs, m);
+                if (plan) plan->contractions.emplace_back(u, v);
                 changed = true;
                 break;
             }
         }
     }
     std::vector<Gate> out;
-    for (int v : dag.topo_order()) out.push_back(dag.nodes_[v].g);
+    const std::vector<int> order = dag.topo_order();
+    if (plan) plan->order = order;
+    for (int v : order) out.push_back(dag.nodes_[v].g);
+    return out;
+}
+
+// Replay a recorded plan on gates with the same qubit sets: Algorithm 2's decisions
+// depend only on the qubits, so this yields the schedule fuse_gates would produce, with
+// the same products computed in the same order.
+std::vector<Gate> replay_fusion(std::vector<Gate> nodes, const FusePlan &plan) {
+    for (const auto &uv : plan.contractions) {
+        Gate &gu = nodes[uv.first];
+        const Gate &gv = nodes[uv.second];
+        uint32_t qs[2 * SV_MAX_K];
+        const uint32_t m = Dag::union_qubits(gu, gv, qs);
+        gu = fused_product(gu, gv, qs, m);
+    }
+    std::vector<Gate> out;
+    out.reserve(plan.order.size());
+    for (int v : plan.order) out.push_back(std::move(nodes[v]));
     return out;
 }
 

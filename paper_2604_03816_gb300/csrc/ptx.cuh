@@ -59,6 +59,20 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Potentially blocking test (no suspend-time hint): the thread may be suspended until the
+// phase completes or a hardware time limit passes, instead of polling shared memory.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Wait for a phase, giving up when *abort is set by another role or after limit_ns (then
 // setting *abort).  Returns false when it gave up.
 __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity,
@@ -67,8 +81,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity
     if (mbar_test_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
     while (true) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_test_wait(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if (*abort) return false;
         if (globaltimer_ns() - t0 > limit_ns) {
             *abort = 1;
@@ -136,6 +149,37 @@ __device__ __forceinline__ void bulk_wait_all() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+
+// Tile addressing for the warp that moves a tile: lane i (< 2^h) owns segment i of every
+// tile, whose offset from the tile's base it computes once; the tile base deposits the
+// tile index around the h high target bits.  The high-target positions live in
+// registers, so no per-segment constant-bank loads remain on the copy path.
+struct SegLanes {
+    uint32_t L, h;
+    uint32_t hi[5];
+    unsigned long long my_off;   // this lane's segment offset (amplitudes)
+
+    __device__ __forceinline__ void init(uint32_t L_, uint32_t h_, const uint32_t *hi_, uint32_t lane) {
+        L = L_;
+        h = h_;
+        my_off = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            hi[j] = j < (int)h ? hi_[j] : 0u;
+            if (j < (int)h && ((lane >> j) & 1u)) my_off |= 1ull << hi[j];
+        }
+    }
+    __device__ __forceinline__ unsigned long long base(unsigned long long t) const {
+        unsigned long long b = t << L;
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            if (j < (int)h) {
+                const unsigned long long lo = b & ((1ull << hi[j]) - 1ull);
+                b = ((b >> hi[j]) << (hi[j] + 1)) | lo;
+            }
+        return b;
+    }
+};
 
 // Insert a zero bit at position p of x (bits >= p move up by one).
 __device__ __forceinline__ uint64_t insert_zero64(uint64_t x, uint32_t p) {

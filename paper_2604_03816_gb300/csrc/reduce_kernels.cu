@@ -379,7 +379,9 @@ sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const
     return SV_OK;
 }
 
-sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
+// Enqueue the top-64 search and asynchronous copies of the 64 (p, index) pairs, best
+// first, into host_p / host_i (pinned memory for a truly asynchronous copy).
+sv_status enqueue_topk(sv_state *s, double *host_p, unsigned long long *host_i) {
     const unsigned long long N = 1ull << s->n;
     const int threads = 256, warps_per_block = threads / 32;
     int blocks = std::min(s->num_sms * 2, TOPK_MAX_WARPS / warps_per_block);
@@ -397,10 +399,18 @@ sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
     SV_CUDA(cudaGetLastError());
     svk::topk_pass2<<<1, 32, 0, s->stream>>>(cp, ci, nwarps * 64, op, oi);
     SV_CUDA(cudaGetLastError());
+    SV_CUDA(cudaMemcpyAsync(host_p, op, 64 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    SV_CUDA(cudaMemcpyAsync(host_i, oi, 64 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            s->stream));
+    return SV_OK;
+}
+
+sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
+    const unsigned long long N = 1ull << s->n;
     double hp[64];
     unsigned long long hi[64];
-    SV_CUDA(cudaMemcpyAsync(hp, op, sizeof(hp), cudaMemcpyDeviceToHost, s->stream));
-    SV_CUDA(cudaMemcpyAsync(hi, oi, sizeof(hi), cudaMemcpyDeviceToHost, s->stream));
+    sv_status st = enqueue_topk(s, hp, hi);
+    if (st != SV_OK) return st;
     SV_CUDA(cudaStreamSynchronize(s->stream));
     const uint32_t m = (uint32_t)std::min<unsigned long long>(k, N);
     for (uint32_t j = 0; j < m; ++j) {

@@ -212,10 +212,53 @@ sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_
     if (!c) return set_error(SV_ERR_OOM, "sv_fuse: host allocation failed");
     c->n = n;
     try {
-        c->gates = fuse_gates(in, n, max_k);
+        c->max_k = max_k;
+        c->in_k.reserve(in.size());
+        c->in_t.reserve(in.size() * SV_MAX_K);
+        for (const Gate &g : in) {
+            c->in_k.push_back(g.k);
+            for (uint32_t j = 0; j < SV_MAX_K; ++j) c->in_t.push_back(j < g.k ? g.t[j] : 0);
+        }
+        c->gates = fuse_gates(in, n, max_k, &c->plan);
     } catch (const std::bad_alloc &) {
         delete c;
         return set_error(SV_ERR_OOM, "sv_fuse: host allocation failed");
+    }
+    *out = c;
+    return SV_OK;
+}
+
+sv_status sv_fuse_like(const sv_circuit *pattern, const sv_gate *gates, size_t ngates, sv_circuit **out) {
+    clear_error();
+    if (!pattern || !out || (ngates && !gates)) return set_error(SV_ERR_ARG, "sv_fuse_like: null argument");
+    *out = nullptr;
+    if (ngates != pattern->in_k.size())
+        return set_error(SV_ERR_ARG, "sv_fuse_like: gate count differs from the pattern's");
+    std::vector<Gate> in;
+    in.reserve(ngates);
+    for (size_t i = 0; i < ngates; ++i) {
+        sv_status st = validate_gate(&gates[i], pattern->n, "sv_fuse_like");
+        if (st != SV_OK) return st;
+        in.push_back(sorted_gate(gates[i].k, gates[i].targets, gates[i].u));
+        const Gate &g = in.back();
+        bool same = g.k == pattern->in_k[i];
+        for (uint32_t j = 0; same && j < g.k; ++j) same = g.t[j] == pattern->in_t[i * SV_MAX_K + j];
+        if (!same)
+            return set_error(SV_ERR_ARG, "sv_fuse_like: gate " + std::to_string(i) +
+                                             " acts on other qubits than the pattern's");
+    }
+    sv_circuit *c = new (std::nothrow) sv_circuit();
+    if (!c) return set_error(SV_ERR_OOM, "sv_fuse_like: host allocation failed");
+    try {
+        c->n = pattern->n;
+        c->max_k = pattern->max_k;
+        c->in_k = pattern->in_k;
+        c->in_t = pattern->in_t;
+        c->plan = pattern->plan;
+        c->gates = replay_fusion(std::move(in), pattern->plan);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return set_error(SV_ERR_OOM, "sv_fuse_like: host allocation failed");
     }
     *out = c;
     return SV_OK;

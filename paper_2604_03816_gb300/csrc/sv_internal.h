@@ -28,14 +28,29 @@ struct Gate {
 // Relabel a gate's local bits so that its targets are ascending (same operator).
 Gate sorted_gate(uint32_t k, const uint32_t *targets, const double *u);
 
-// Algorithm 2 over sorted gates (fuse.cpp).
-std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k);
+// The decisions of one run of Algorithm 2: contractions (u absorbs v) in order and the
+// final topological order of the surviving vertices.
+struct FusePlan {
+    std::vector<std::pair<int, int>> contractions;
+    std::vector<int> order;
+};
+
+// Algorithm 2 over sorted gates (fuse.cpp); records its decisions in *plan if given.
+std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k,
+                             FusePlan *plan = nullptr);
+// Apply a recorded plan to gates with the same qubit sets (fuse.cpp).
+std::vector<Gate> replay_fusion(std::vector<Gate> nodes, const FusePlan &plan);
 
 }  // namespace svi
 
 struct sv_circuit {
     uint32_t n = 0;
     std::vector<svi::Gate> gates;
+    // how it was fused, for sv_fuse_like: input qubit sets and the recorded plan
+    uint32_t max_k = 0;
+    std::vector<uint32_t> in_k;
+    std::vector<uint32_t> in_t;       // SV_MAX_K per input gate, sorted
+    svi::FusePlan plan;
 };
 
 // Device workspace layout (bytes), carved from one allocation.
@@ -68,6 +83,20 @@ struct sv_state {
     uint32_t policy = 0;        // SV_POLICY_* flags (kernel selection)
 };
 
+// One batched launch: gate k/t applied to `states` consecutive states at psi with
+// per-state matrices at utab (batch.cu).
+struct sv_batch_launch {
+    sv_dtype dtype = SV_C64;
+    uint32_t k = 0, n = 0;
+    uint32_t t[SV_MAX_K] = {0, 0, 0, 0, 0};
+    uint32_t states = 0;
+    void *psi = nullptr;
+    const void *utab = nullptr;
+    int *err = nullptr;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+};
+
 namespace svi {
 // ---- kernels (apply_kernels.cu / reduce_kernels.cu); all enqueue on s->stream ----
 sv_status launch_apply(sv_state *s, const Gate &g);
@@ -78,6 +107,7 @@ sv_status launch_probs(sv_state *s, void *dev_out);
 sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const double *c,
                         size_t nterms, double *host_out);
 sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
+sv_status enqueue_topk(sv_state *s, double *host_p, unsigned long long *host_i);
 sv_status launch_widen(sv_state *s, const void *src_c64, void *dst_c128);
 sv_status launch_set_one(sv_state *s, uint64_t x);
 sv_status check_device_error(sv_state *s);   // synchronises; reads and clears the error word

@@ -35,6 +35,11 @@ EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
            "sv_expect_noalloc"]
+EXPORTS += ["sv_fuse_like"]
+EXPORTS += ["sv_server_create", "sv_server_submit", "sv_server_poll", "sv_server_get_stats",
+            "sv_server_destroy"]
+EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_get_state",
+            "sv_batch_apply", "sv_batch_expect", "sv_batch_sync", "sv_batch_tune"]
 SV_POLICY_NO_TENSOR_CORES = 1
 
 
@@ -61,6 +66,44 @@ class sv_apply_report(ctypes.Structure):
                 ("bytes", ctypes.c_uint64), ("apply_ms", ctypes.c_double)]
 
 
+class sv_batch_opts(ctypes.Structure):
+    _fields_ = [("chunk_states", ctypes.c_uint32), ("l2_bytes", ctypes.c_size_t),
+                ("no_graph", ctypes.c_uint32), ("timing", ctypes.c_uint32)]
+
+
+class sv_batch_report(ctypes.Structure):
+    _fields_ = [("passes", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("bytes", ctypes.c_uint64), ("chunk_states", ctypes.c_uint32),
+                ("graph_reused", ctypes.c_uint32), ("apply_ms", ctypes.c_double)]
+
+
+class sv_tune_result(ctypes.Structure):
+    _fields_ = [("best_k", ctypes.c_uint32), ("l2_bytes", ctypes.c_size_t),
+                ("best_ms", ctypes.c_double), ("ms", ctypes.c_double * (SV_MAX_K + 1)),
+                ("cached", ctypes.c_uint32)]
+
+
+class sv_server_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_uint32),
+                ("topk", ctypes.c_uint32), ("max_k", ctypes.c_uint32),
+                ("fuse_threads", ctypes.c_uint32)]
+
+
+class sv_server_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("dtype_used", ctypes.c_int32),
+                ("n", ctypes.c_uint32), ("k", ctypes.c_uint32), ("passes", ctypes.c_uint64),
+                ("idx", ctypes.c_uint64 * 64), ("p", ctypes.c_double * 64),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class sv_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("active", ctypes.c_uint32),
+                ("in_use_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("now", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _u32, _u64, _i32 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -75,6 +118,7 @@ _sig = {
     "sv_get_state": [_vp, _vp, _i32],
     "sv_fuse": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32, ctypes.POINTER(_vp)],
     "sv_circuit_free": [_vp],
+    "sv_fuse_like": [_vp, ctypes.POINTER(sv_gate), ctypes.c_size_t, ctypes.POINTER(_vp)],
     "sv_circuit_size": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_u32)],
     "sv_circuit_gate": [_vp, ctypes.c_size_t, ctypes.POINTER(_u32), ctypes.POINTER(_u32), _dp],
     "sv_choose_dtype": [_u32, _u64, ctypes.c_double, ctypes.POINTER(_i32), _dp],
@@ -86,6 +130,23 @@ _sig = {
     "sv_topk": [_vp, _u32, ctypes.POINTER(_u64), _dp],
     "sv_sync": [_vp],
     "sv_set_policy": [_vp, _u32],
+    "sv_server_create": [ctypes.POINTER(sv_server_config), ctypes.POINTER(_vp)],
+    "sv_server_submit": [_vp, _u32, _i32, ctypes.POINTER(sv_gate), ctypes.c_size_t,
+                         ctypes.POINTER(_u64)],
+    "sv_server_poll": [_vp, ctypes.POINTER(sv_server_result), ctypes.c_size_t,
+                       ctypes.POINTER(ctypes.c_size_t), _i32],
+    "sv_server_get_stats": [_vp, ctypes.POINTER(sv_server_stats)],
+    "sv_server_destroy": [_vp],
+    "sv_batch_alloc": [_u32, _i32, _u32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)],
+    "sv_batch_free": [_vp],
+    "sv_batch_set_basis": [_vp, _u64],
+    "sv_batch_get_state": [_vp, _u32, _vp, _i32],
+    "sv_batch_apply": [_vp, ctypes.POINTER(_vp), ctypes.POINTER(sv_batch_opts),
+                       ctypes.POINTER(sv_batch_report)],
+    "sv_batch_expect": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp, ctypes.c_size_t, _dp],
+    "sv_batch_sync": [_vp],
+    "sv_batch_tune": [_vp, ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32,
+                      ctypes.POINTER(sv_tune_result)],
     "sv_expect_noalloc": [_vp, _u32, _i32, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp,
                           ctypes.c_size_t, _vp, _vp],
 }
@@ -163,10 +224,19 @@ class Circuit:
         return sv_circuit_size(self)[0]
 
 
-def sv_fuse(gates: Sequence[Tuple[Sequence[int], np.ndarray]], n: int, max_k: int) -> Circuit:
-    ga = GateArray(gates)
+def sv_fuse(gates, n: int, max_k: int) -> Circuit:
+    """gates: [(targets, U)] or a prebuilt GateArray."""
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
     h = _vp()
     _check(_lib.sv_fuse(ga.arr, ga.n, n, max_k, ctypes.byref(h)))
+    return Circuit(h.value)
+
+
+def sv_fuse_like(pattern: Circuit, gates) -> Circuit:
+    """gates: [(targets, U)] or a prebuilt GateArray, same qubits as the pattern's input."""
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    h = _vp()
+    _check(_lib.sv_fuse_like(pattern.handle, ga.arr, ga.n, ctypes.byref(h)))
     return Circuit(h.value)
 
 
@@ -357,3 +427,139 @@ def sv_set_policy(s: State, flags: int) -> None:
 
 def sv_sync(s: State) -> None:
     _check(_lib.sv_sync(s.handle))
+
+
+# --------------------------------------------------------------------------- batches
+
+class Batch:
+    def __init__(self, handle: int, n: int, dtype: int, count: int, keep=None):
+        self.handle, self.n, self.dtype, self.count, self.keep = handle, n, dtype, count, keep
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.sv_batch_free(self.handle)
+            self.handle = None
+
+    def free(self):
+        if self.handle:
+            _check(_lib.sv_batch_free(self.handle))
+            self.handle = None
+
+
+def sv_batch_alloc(n: int, dtype: int, count: int, dev_buf=None, nbytes: int = 0,
+                   stream=None) -> Batch:
+    keep, ptr = None, None
+    if dev_buf is not None:
+        keep, ptr = dev_buf, int(dev_buf.data_ptr())
+        nbytes = nbytes or int(dev_buf.numel() * dev_buf.element_size())
+    h = _vp()
+    _check(_lib.sv_batch_alloc(n, dtype, count, ptr, nbytes, _stream_ptr(stream), ctypes.byref(h)))
+    return Batch(h.value, n, dtype, count, keep)
+
+
+def sv_batch_free(b: Batch) -> None:
+    b.free()
+
+
+def sv_batch_set_basis(b: Batch, x: int) -> None:
+    _check(_lib.sv_batch_set_basis(b.handle, x))
+
+
+def sv_batch_get_state(b: Batch, i: int) -> np.ndarray:
+    a = np.empty(1 << b.n, dtype=_np_dtype(b.dtype))
+    _check(_lib.sv_batch_get_state(b.handle, i, a.ctypes.data, 0))
+    return a
+
+
+def sv_batch_apply(b: Batch, circuits: Sequence[Circuit], chunk_states: int = 0,
+                   l2_bytes: int = 0, no_graph: bool = False, timing: bool = False) -> dict:
+    arr = (_vp * len(circuits))(*[c.handle for c in circuits])
+    assert len(circuits) == b.count
+    opts = sv_batch_opts(chunk_states, l2_bytes, int(bool(no_graph)), int(bool(timing)))
+    rep = sv_batch_report()
+    _check(_lib.sv_batch_apply(b.handle, arr, ctypes.byref(opts), ctypes.byref(rep)))
+    return {"passes": rep.passes, "launches": rep.launches, "bytes": rep.bytes,
+            "chunk_states": rep.chunk_states, "graph_reused": rep.graph_reused,
+            "apply_ms": rep.apply_ms}
+
+
+def sv_batch_expect(b: Batch, xmask, zmask, coef) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(list(xmask), dtype=np.uint64))
+    z = np.ascontiguousarray(np.asarray(list(zmask), dtype=np.uint64))
+    c = np.ascontiguousarray(np.asarray(list(coef), dtype=np.float64))
+    out = np.zeros(b.count, dtype=np.float64)
+    u64p = ctypes.POINTER(_u64)
+    _check(_lib.sv_batch_expect(b.handle, x.ctypes.data_as(u64p), z.ctypes.data_as(u64p), _ptr(c),
+                                x.size, _ptr(out)))
+    return out
+
+
+def sv_batch_sync(b: Batch) -> None:
+    _check(_lib.sv_batch_sync(b.handle))
+
+
+def sv_batch_tune(b: Batch, gates: Sequence[Tuple[Sequence[int], np.ndarray]], kmin: int = 1,
+                  kmax: int = 4) -> dict:
+    ga = GateArray(gates)
+    r = sv_tune_result()
+    _check(_lib.sv_batch_tune(b.handle, ga.arr, ga.n, kmin, kmax, ctypes.byref(r)))
+    return {"best_k": r.best_k, "l2_bytes": r.l2_bytes, "best_ms": r.best_ms,
+            "ms": {k: r.ms[k] for k in range(kmin, kmax + 1)}, "cached": r.cached}
+
+
+# --------------------------------------------------------------------------- serving
+
+class Server:
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.sv_server_destroy(self.handle)
+            self.handle = None
+
+    def destroy(self):
+        if self.handle:
+            _check(_lib.sv_server_destroy(self.handle))
+            self.handle = None
+
+
+def sv_server_create(budget_bytes: int = 0, max_slots: int = 0, topk: int = 0, max_k: int = 0,
+                     fuse_threads: int = 0) -> Server:
+    cfg = sv_server_config(budget_bytes, max_slots, topk, max_k, fuse_threads)
+    h = _vp()
+    _check(_lib.sv_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return Server(h.value)
+
+
+def sv_server_submit(srv: Server, n: int, dtype: int, gates) -> int:
+    """gates: a GateArray (prebuilt) or [(targets, U)]."""
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    rid = _u64()
+    _check(_lib.sv_server_submit(srv.handle, n, dtype, ga.arr, ga.n, ctypes.byref(rid)))
+    return rid.value
+
+
+def _result_dict(r: sv_server_result) -> dict:
+    k = r.k
+    return {"id": r.id, "status": r.status, "dtype_used": r.dtype_used, "n": r.n, "k": k,
+            "passes": r.passes, "idx": np.array(r.idx[:k], dtype=np.uint64),
+            "p": np.array(r.p[:k], dtype=np.float64), "t_submit": r.t_submit,
+            "t_admit": r.t_admit, "t_done": r.t_done}
+
+
+def sv_server_poll(srv: Server, cap: int = 256, wait_ms: int = 0) -> list:
+    buf = (sv_server_result * cap)()
+    nout = ctypes.c_size_t()
+    _check(_lib.sv_server_poll(srv.handle, buf, cap, ctypes.byref(nout), wait_ms))
+    return [_result_dict(buf[i]) for i in range(nout.value)]
+
+
+def sv_server_get_stats(srv: Server) -> dict:
+    st = sv_server_stats()
+    _check(_lib.sv_server_get_stats(srv.handle, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in sv_server_stats._fields_}
+
+
+def sv_server_destroy(srv: Server) -> None:
+    srv.destroy()

@@ -1,0 +1,82 @@
+"""Continuous-batching server: admission by HBM budget, overlap, and results that do
+not depend on the other requests in flight."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(seed=0, count=12):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(8, 19))
+        d = int(rng.integers(3, 12))
+        dt = 0 if rng.uniform() < 0.7 else 1
+        out.append((n, dt, W.brickwork(n, d, seed=int(rng.integers(0, 2**31)))))
+    return out
+
+
+def _drain(sv, srv, expected, timeout_s=120):
+    got = {}
+    t0 = time.time()
+    while len(got) < expected:
+        for r in sv.sv_server_poll(srv, 256, 50):
+            got[r["id"]] = r
+        assert time.time() - t0 < timeout_s, "server did not finish"
+    return got
+
+
+def test_results_alone_equal_results_in_the_mix(gpu):
+    sv = gpu
+    reqs = _requests()
+    arrays = [sv.GateArray(sv.gates_from_specs(g)) for _, _, g in reqs]
+    srv = sv.sv_server_create(max_slots=8, max_k=4)
+    alone = []
+    for (n, dt, _), ga in zip(reqs, arrays):
+        rid = sv.sv_server_submit(srv, n, dt, ga)
+        alone.append(_drain(sv, srv, 1)[rid])
+    ids = [sv.sv_server_submit(srv, n, dt, ga) for (n, dt, _), ga in zip(reqs, arrays)]
+    mix = _drain(sv, srv, len(ids))
+    srv.destroy()
+    for (n, dt, g), a, rid in zip(reqs, alone, ids):
+        m = mix[rid]
+        assert a["status"] == 0 and m["status"] == 0
+        assert np.array_equal(a["idx"], m["idx"]) and np.array_equal(a["p"], m["p"])
+        assert a["t_submit"] <= a["t_admit"] <= a["t_done"]
+        # and the answer is right: a valid top-64 of the oracle's distribution
+        p_ref = oracle.probs(oracle.simulate(n, g))
+        tol = 1e-5 if dt == 0 else 1e-12
+        assert oracle.topk_valid(m["idx"], p_ref, 64, tol)
+        assert np.max(np.abs(m["p"] - p_ref[m["idx"].astype(np.int64)])) < tol
+
+
+def test_admission_respects_the_budget_and_rejects_what_never_fits(gpu):
+    sv = gpu
+    state18 = (8 << 18) + 16 * 16 * 8 + 4 * 1024 * 1024 + 64 * 1024   # about one 18q c64 request
+    budget = 2 * state18 + (1 << 20)
+    srv = sv.sv_server_create(budget_bytes=budget, max_slots=8, max_k=2)
+    ga = sv.GateArray(sv.gates_from_specs(W.brickwork(18, 20)))
+    ids = [sv.sv_server_submit(srv, 18, 0, ga) for _ in range(6)]
+    big = sv.sv_server_submit(srv, 24, 0, sv.GateArray(sv.gates_from_specs(W.brickwork(24, 2))))
+    peak = 0
+    got = {}
+    t0 = time.time()
+    while len(got) < len(ids) + 1:
+        st = sv.sv_server_get_stats(srv)
+        assert st["in_use_bytes"] <= budget
+        peak = max(peak, st["active"])
+        for r in sv.sv_server_poll(srv, 64, 5):
+            got[r["id"]] = r
+        assert time.time() - t0 < 120
+    srv.destroy()
+    assert peak <= 2
+    assert got[big]["status"] == 2                        # SV_ERR_OOM: can never fit
+    assert all(got[i]["status"] == 0 for i in ids)
+    ref = got[ids[0]]
+    assert all(np.array_equal(got[i]["idx"], ref["idx"]) for i in ids)

@@ -110,3 +110,21 @@ def test_argument_errors_are_reported(svlib):
         svlib.sv_alloc(0)                                   # n out of range, no GPU call
     with pytest.raises(svlib.SvError):
         svlib.sv_alloc(35)
+
+
+def test_fuse_like_equals_fuse(svlib):
+    # Algorithm 2's decisions depend on the qubits only: replaying them on new angles
+    # gives exactly what a fresh fusion gives.
+    for n, k in ((16, 4), (22, 4), (12, 5), (9, 2)):
+        pat = svlib.sv_fuse(svlib.gates_from_specs(W.hea(n, 6, seed=1)), n, k)
+        for seed in (2, 3):
+            gl = svlib.gates_from_specs(W.hea(n, 6, seed=seed))
+            a = svlib.sv_fuse(gl, n, k)
+            b = svlib.sv_fuse_like(pat, gl)
+            assert len(a) == len(b)
+            for i in range(len(a)):
+                ta, ua = svlib.sv_circuit_gate(a, i)
+                tb, ub = svlib.sv_circuit_gate(b, i)
+                assert ta == tb and np.array_equal(ua, ub)
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse_like(pat, svlib.gates_from_specs(W.brickwork(9, 2)))
