@@ -13,12 +13,16 @@
 // norm per pass).  Instead each operand is cut into three 9-bit integer slices on a
 // fixed-point grid -- per row of A (scale 2^{8-e}, e = exponent of the row's largest
 // component) and for all of B -- so that x = (a1 + a2 2^-9 + a3 2^-18) / s.  The
-// slices are exact in FP16, every product is an integer below 2^16, and the three sums
-//     D0 = A1 B1,  D1 = A1 B2 + A2 B1,  D2 = A1 B3 + A2 B2 + A3 B1
-// stay below 2^24 over K <= 64, so the tensor cores (kind::f16, FP32 accumulators in
-// TMEM) compute them exactly.  The epilogue combines them with round-to-nearest,
-// out = (D0 + (D1 + D2 2^-9) 2^-9) / (s s_B): unbiased, about FP32 accuracy relative to
-// the row's largest amplitude (the dropped slice products are below 2^-27 of it).
+// slices are exact in FP16 and every product of integer slices is below 2^16, so
+//     D0  = A1 B1                                      (below 2^22: exact in FP32)
+//     D12 = A1 B2 + A2 B1 + 2^-9 (A1 B3 + A2 B2 + A3 B1)
+// are accumulated by the tensor cores (kind::f16, FP32 accumulators in TMEM); the
+// 2^-9-scaled slices (B3, B2 and A3 times 2^-9) are also exact in FP16.  D0, which
+// carries the leading 2^22 of the result, is exact; D12 sits 2^-9 below it, so the
+// truncation of its accumulation costs about 2^-31 of the output per step -- the error
+// stays unbiased to well below FP32 rounding.  The epilogue forms
+// out = (D0 + 2^-9 D12) / (s s_B) with round-to-nearest (the dropped slice products are
+// below 2^-27 of the row's largest amplitude).
 //
 // One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
 //   warp 4 (one thread)  TMA producer: 1-D bulk loads of each tile's 2^h segments into a
@@ -58,15 +62,17 @@ struct TcShape {
     static constexpr uint32_t TB = K + 7;             // tile bits
     static constexpr uint32_t TILE_BYTES = ROWS * D * 8u;
     static constexpr uint32_t B_BYTES = KD * KD * 2u;     // one FP16 slice of B
+    static constexpr uint32_t NB = 4;                     // B1, B2, B3 * 2^-9, B2 * 2^-9
     static constexpr uint32_t SBO = (KD / 8u) * 128u;     // 8-row group stride of B
-    static constexpr uint32_t NS = K == 5 ? 4u : 8u;      // raw stages
+    static constexpr uint32_t NS = K == 5 ? 3u : 8u;      // raw stages
     static constexpr uint32_t NOUT = 2u;                  // output staging tiles
-    static constexpr uint32_t ACC = 3u * KD;              // TMEM columns of one D set
+    static constexpr uint32_t ACC = 2u * KD;              // TMEM columns of one D set (D0, D12)
     static constexpr uint32_t A_COLS = KD / 2u;           // TMEM columns of one A slice
-    static constexpr uint32_t A_COL0 = 2u * ACC;          // first column of A
+    static constexpr uint32_t A_SET = 3u * A_COLS;        // one A buffer (three slices)
+    static constexpr uint32_t A_COL0 = 2u * ACC;          // first column of the A buffers
     static constexpr uint32_t TMEM_COLS = K == 5 ? 512u : 256u;
-    static_assert(A_COL0 + 3u * A_COLS <= TMEM_COLS, "TMEM layout");
-    static constexpr uint32_t OFF_RAW = 3u * B_BYTES;
+    static_assert(A_COL0 + 2u * A_SET <= TMEM_COLS, "TMEM layout");
+    static constexpr uint32_t OFF_RAW = NB * B_BYTES;
     static constexpr uint32_t OFF_OUT = OFF_RAW + NS * TILE_BYTES;
     static constexpr uint32_t SMEM = OFF_OUT + NOUT * TILE_BYTES;
     static constexpr uint32_t THREADS = 320;              // 10 warps
@@ -95,7 +101,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
     constexpr uint32_t D = S::D, KD = S::KD, NS = S::NS, NOUT = S::NOUT;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
-    __shared__ __align__(8) unsigned long long a_full, a_empty, d_full[2], d_empty[2];
+    __shared__ __align__(8) unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2];
     __shared__ __align__(8) unsigned long long scale_full[4];   // row scales, tile j -> j & 3
     __shared__ float row_scale[4][128];
     __shared__ uint32_t tmem_slot;
@@ -119,9 +125,9 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        mbar_init(smem_u32(&a_full), 1);
-        mbar_init(smem_u32(&a_empty), 1);
         for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&a_full[b]), 1);
+            mbar_init(smem_u32(&a_empty[b]), 1);
             mbar_init(smem_u32(&d_full[b]), 1);
             mbar_init(smem_u32(&d_empty[b]), 1);
         }
@@ -131,9 +137,11 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
     }
     for (uint32_t e = tid; e < KD * KD; e += blockDim.x) {
         const uint32_t n = e / KD, kk = e % KD, off = kmajor_off16(n, kk, S::SBO);
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-            *reinterpret_cast<__half *>(sB + j * S::B_BYTES + off) = __int2half_rn(a.b[j][e]);
+        *reinterpret_cast<__half *>(sB + 0 * S::B_BYTES + off) = __int2half_rn(a.b[0][e]);
+        *reinterpret_cast<__half *>(sB + 1 * S::B_BYTES + off) = __int2half_rn(a.b[1][e]);
+        // exact: integers below 2^9 times 2^-9
+        *reinterpret_cast<__half *>(sB + 2 * S::B_BYTES + off) = __float2half_rn(a.b[2][e] * (1.f / 512.f));
+        *reinterpret_cast<__half *>(sB + 3 * S::B_BYTES + off) = __float2half_rn(a.b[1][e] * (1.f / 512.f));
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -188,27 +196,27 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             uint32_t j = 0;
             for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
                 const uint32_t b = j & 1u, u = j >> 1;
-                if (!mbar_wait_or_abort(smem_u32(&a_full), j & 1u, abort)) break;
+                if (!mbar_wait_or_abort(smem_u32(&a_full[b]), u & 1u, abort)) break;
                 if (!mbar_wait_or_abort(smem_u32(&d_empty[b]), (u & 1u) ^ 1u, abort)) break;
                 tc_fence_after();
-                const uint32_t A0 = tmem + S::A_COL0;
+                const uint32_t A0 = tmem + S::A_COL0 + b * S::A_SET;
                 const uint32_t dset = tmem + b * S::ACC;
-                // (accumulator, A slice, B slice): D0 = A1B1, D1 = A1B2 + A2B1,
-                // D2 = A1B3 + A2B2 + A3B1
+                // (accumulator, A slice, B slice): D0 = A1 B1; D12 = A1 B2 + A2 B1 +
+                // A1 (B3 2^-9) + A2 (B2 2^-9) + (A3 2^-9) B1   [B slices: B1, B2, B3s, B2s]
                 const uint32_t prod[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0},
-                                             {2, 0, 2}, {2, 1, 1}, {2, 2, 0}};
+                                             {1, 0, 2}, {1, 1, 3}, {1, 2, 0}};
 #pragma unroll
                 for (int p = 0; p < 6; ++p) {
                     const uint32_t Aa = A0 + prod[p][1] * S::A_COLS;
                     const uint32_t Bb = B0 + prod[p][2] * S::B_BYTES;
-                    const bool first_in_acc = (p == 0 || p == 1 || p == 3);
+                    const bool first_in_acc = (p == 0 || p == 1);
 #pragma unroll
                     for (uint32_t ks = 0; ks < KD / 16; ++ks)
                         mma_f16_tmem_a(dset + prod[p][0] * KD, Aa + ks * 8u,
                                        smem_desc(Bb + ks * 256u, 128u, S::SBO), idesc,
                                        (first_in_acc && ks == 0) ? 0u : 1u);
                 }
-                mma_commit(smem_u32(&a_empty));
+                mma_commit(smem_u32(&a_empty[b]));
                 mma_commit(smem_u32(&d_full[b]));
             }
         }
@@ -238,11 +246,12 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             frexpf(m, &ex);                       // m < 2^ex (m = 0: ex = 0)
             ex = max(ex, -100);                   // keep 2^(8-ex) finite
             const float scale = ldexpf(1.f, 8 - ex);   // |x * scale| < 256
-            ok = mbar_wait_or_abort(smem_u32(&a_empty), (j & 1u) ^ 1u, abort);
+            const uint32_t ab = j & 1u;
+            ok = mbar_wait_or_abort(smem_u32(&a_empty[ab]), ((j >> 1) & 1u) ^ 1u, abort);
             if (!named_bar_and(1, 128, ok)) break;
             tc_fence_after();
             // slot j & 3 was last read by the epilogue of tile j - 4, which finished before
-            // the MMAs of tile j - 1 were issued, whose completion released a_empty
+            // the MMAs of tile j - 2 were issued, whose completion released a_empty[ab]
             row_scale[j & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
             // three 9-bit integer slices, one FP16 pair (re, im) per 32-bit TMEM column
             uint32_t w1[D], w2[D], w3[D];
@@ -255,9 +264,9 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
                 const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
                 w1[c] = pack_half2(r1, i1);
                 w2[c] = pack_half2(r2, i2);
-                w3[c] = pack_half2(r3, i3);
+                w3[c] = pack_half2(r3 * (1.f / 512.f), i3 * (1.f / 512.f));   // A3 2^-9, exact
             }
-            const uint32_t arow = tmem + S::A_COL0 + ((warp * 32u) << 16);
+            const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + ((warp * 32u) << 16);
             if constexpr (D == 32) {
                 tmem_st32(arow, w1);
                 tmem_st32(arow + S::A_COLS, w2);
@@ -270,7 +279,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             tc_fence_before();
             named_bar(1, 128);
             if (row == 0) {
-                mbar_arrive(smem_u32(&a_full));
+                mbar_arrive(smem_u32(&a_full[ab]));
                 mbar_arrive(smem_u32(&scale_full[j & 3u]));
             }
         }
@@ -298,15 +307,13 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16);
 #pragma unroll
             for (uint32_t c0 = 0; c0 < KD; c0 += 32) {
-                float d0[32], d1[32], d2[32];
+                float d0[32], d12[32];
                 tmem_ld32(lane_addr + c0, d0);
-                tmem_ld32(lane_addr + KD + c0, d1);
-                tmem_ld32(lane_addr + 2 * KD + c0, d2);
+                tmem_ld32(lane_addr + KD + c0, d12);
 #pragma unroll
                 for (uint32_t i = 0; i < 32; i += 2) {
-                    const float re = (d0[i] + (d1[i] + d2[i] * (1.f / 512.f)) * (1.f / 512.f)) * osc;
-                    const float im =
-                        (d0[i + 1] + (d1[i + 1] + d2[i + 1] * (1.f / 512.f)) * (1.f / 512.f)) * osc;
+                    const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
+                    const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
                     out[gbase | coff[(c0 + i) / 2]] = make_float2(re, im);
                 }
             }
