@@ -35,10 +35,10 @@ METRIC = ("fused-gate HBM GB/s & circuits/s at 28–33q vs unfused c128; "
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic of one apply pass at 30 qubits complex64, fused width 5, from the ncu
-# capture summarised in profiles/apply_tile_c64_30q.md; valid only for the kernel source
-# with this sha256 prefix (null otherwise).
-TRAFFIC = {"sha256_prefix": None, "bytes_per_launch": None}
+# DRAM traffic of one tensor-core pass (apply_tc<5>) from the ncu capture summarised in
+# profiles/apply_tc5_c64_27q_ncu.md (2.087 GB at 27 qubits), scaled by 2^3 to the 30-qubit
+# launch; valid only while the kernel sources hash to this prefix (null otherwise).
+TRAFFIC = {"sha256_prefix": "f617682c54ae1bd9", "bytes_per_launch": 2.0865e9 * 8, "n": 30}
 
 
 def parse():
@@ -75,7 +75,7 @@ def dist_info():
 
 def kernel_sha():
     h = hashlib.sha256()
-    for f in ("apply_kernels.cu", "ptx.cuh"):
+    for f in ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"):
         with open(os.path.join(ROOT, "paper_2604_03816_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -423,7 +423,8 @@ def main():
         peak, peak_kind = hbm_peak()
         sha = kernel_sha()
         traffic = None
-        if TRAFFIC["sha256_prefix"] and sha.startswith(TRAFFIC["sha256_prefix"]):
+        if (TRAFFIC["sha256_prefix"] and sha.startswith(TRAFFIC["sha256_prefix"])
+                and args.n == TRAFFIC["n"] and args.dtype == "c64"):
             traffic = TRAFFIC["bytes_per_launch"]
 
         if sv.sv_info(state)[1] != dt:          # a promotion widened the state: start over
@@ -488,7 +489,10 @@ def main():
            "max_drift": max(r["drift"] for r in reps),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": traffic,
-                        "kernel": "apply_tile (fused-gate pass)", "peak_kind": peak_kind,
+                        "kernel": "fused-gate pass (apply_tc<5> 63% of GPU time, all apply "
+                                  "kernels 91.5%; profiles/fused_pass_grid30q_k5_launches.md)",
+                        "traffic_source": "apply_tc<5> ncu capture at 27q scaled to 30q",
+                        "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": apply_bytes / passes,
                         "avg_launch_ms": apply_ms / passes},
            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step[0] * args.steps,
