@@ -283,6 +283,8 @@ def run_batched(args):
     gates = {w: [sv.gates_from_specs(g) for g in groups[w]] for w in widths}
     arrays = {w: [sv.GateArray(g) for g in gates[w]] for w in widths}   # the input circuits
     batches, tune = {}, {}
+    import concurrent.futures as cf
+    pool = cf.ThreadPoolExecutor(max_workers=max(1, min(16, (os.cpu_count() or 4))))
     with torch.cuda.stream(stream):
         for w in widths:
             batches[w] = sv.sv_batch_alloc(w, sv.SV_C64, len(groups[w]), stream=stream)
@@ -294,12 +296,15 @@ def run_batched(args):
             for w in widths:
                 t0 = time.perf_counter()
                 # Algorithm 2 once per width; the other circuits of the family replay its
-                # decisions (same qubits, other angles)
+                # decisions (same qubits, other angles), on host threads (the C calls
+                # release the GIL) while the GPU runs the previous width
                 pattern = sv.sv_fuse(arrays[w][0], w, tune[w]["best_k"])
-                circs = [pattern] + [sv.sv_fuse_like(pattern, ga) for ga in arrays[w][1:]]
+                circs = [pattern] + list(pool.map(lambda ga: sv.sv_fuse_like(pattern, ga),
+                                                  arrays[w][1:]))
                 fuse_s += time.perf_counter() - t0
                 sv.sv_batch_set_basis(batches[w], 0)
                 sv.sv_batch_apply(batches[w], circs, l2_bytes=tune[w]["l2_bytes"])
+            for w in widths:
                 xs, zs, cs = W.zz_chain(w)
                 out[w] = sv.sv_batch_expect(batches[w], xs, zs, cs)
             return fuse_s, out

@@ -299,6 +299,8 @@ struct sv_batch {
     std::string graph_key;
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture the graph
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t staged = nullptr;       // the last H2D copy out of utab_host has finished
+    bool staged_pending = false;
 };
 
 namespace svi {
@@ -388,6 +390,7 @@ sv_status sv_batch_alloc(uint32_t n, sv_dtype dtype, uint32_t count, void *dev_b
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         const std::string msg = std::string("sv_batch_alloc: ") + cudaGetErrorString(e);
         sv_batch_free(b);
@@ -415,6 +418,7 @@ sv_status sv_batch_free(sv_batch *b) {
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->staged) cudaEventDestroy(b->staged);
     delete b;
     return SV_OK;
 }
@@ -488,7 +492,7 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
             b->graph_key.clear();
         }
     }
-    SV_CUDA(cudaStreamSynchronize(b->stream));     // staging buffer is free again
+    if (b->staged_pending) SV_CUDA(cudaEventSynchronize(b->staged));   // staging buffer is free
     for (size_t g = 0; g < G; ++g) {
         const size_t d2 = (size_t)1 << (2 * c0->gates[g].k);
         char *dst = static_cast<char *>(b->utab_host) + goff[g];
@@ -510,6 +514,8 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
         }
     }
     SV_CUDA(cudaMemcpyAsync(b->utab, b->utab_host, tab, cudaMemcpyHostToDevice, b->stream));
+    SV_CUDA(cudaEventRecord(b->staged, b->stream));
+    b->staged_pending = true;
 
     const size_t sbytes = elem_bytes_b(b->dtype) << b->n;
     size_t l2 = opts && opts->l2_bytes ? opts->l2_bytes : (size_t(64) << 20);
