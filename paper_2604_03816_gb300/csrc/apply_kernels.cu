@@ -184,6 +184,7 @@ sv_status launch_apply(sv_state *s, const Gate &g) {
     if (g.k < 1 || g.k > SV_MAX_K || g.k > s->n)
         return set_error(SV_ERR_ARG, "apply: gate width out of range");
     if (tc_eligible(s, g)) return launch_apply_tc(s, g);
+    if (tc64_eligible(s, g)) return launch_apply_tc64(s, g);
     if (s->dtype == SV_C64) {
         switch (g.k) {
             case 1: return svk::launch_apply_t<float, 1>(s, g);

@@ -102,6 +102,8 @@ namespace svi {
 sv_status launch_apply(sv_state *s, const Gate &g);
 bool tc_eligible(const sv_state *s, const Gate &g);        // apply_tc.cu
 sv_status launch_apply_tc(sv_state *s, const Gate &g);
+bool tc64_eligible(const sv_state *s, const Gate &g);      // apply_tc64.cu
+sv_status launch_apply_tc64(sv_state *s, const Gate &g);
 sv_status launch_norm(sv_state *s, double *dev_out);     // writes one double on device
 sv_status launch_probs(sv_state *s, void *dev_out);
 sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const double *c,

@@ -1,4 +1,4 @@
-"""Tensor-core (tcgen05, 3xTF32) path for fused k = 4, 5 complex64 gates, against the
+"""Tensor-core (tcgen05, exact FP16 slices) path for fused k = 4, 5 complex64 gates, against the
 oracle and against the CUDA-core kernels on the same inputs."""
 import numpy as np
 import pytest
