@@ -88,14 +88,51 @@ struct TcArgs {
     uint32_t L, h;
     uint32_t hi[SV_MAX_K];
     uint32_t lp[K];
+    // bank-conflict avoidance: the xt lowest targets sit at tile bits below 4; lane l
+    // takes group members in the order c ^ x(l), x(l) = (l >> xs) & (2^xt - 1)
+    uint32_t xs, xt;
 };
+
+// v[c] <- v[c ^ x] for the low xt bits of x: one conditional-swap stage per bit.
+template <int N>
+__device__ __forceinline__ void xor_unpermute(float2 (&v)[N], uint32_t x, uint32_t xt) {
+    constexpr int NBITS = N >= 16 ? 4 : (N >= 8 ? 3 : (N >= 4 ? 2 : 1));
+#pragma unroll
+    for (int j = 0; j < NBITS; ++j) {
+        if (xt > (uint32_t)j) {                       // uniform over the launch
+            const bool f = (x >> j) & 1u;
+#pragma unroll
+            for (int c = 0; c < N; ++c) {
+                if (c & (1 << j)) continue;
+                const float2 lo = v[c], hi = v[c | (1 << j)];
+                v[c] = make_float2(f ? hi.x : lo.x, f ? hi.y : lo.y);
+                v[c | (1 << j)] = make_float2(f ? lo.x : hi.x, f ? lo.y : hi.y);
+            }
+        }
+    }
+}
 
 __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);   // exact: |a|, |b| <= 256 are integers
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-template <int K>
+// XP: the launch has targets among tile bits 0..3 and takes members in the lane's XOR
+// order; otherwise every lane takes them in member order (no permutation code at all).
+// Three 9-bit integer slices of a scaled amplitude (|x scale| < 256): FP16 pairs
+// (re, im) of a1, a2 and a3 2^-9, all exact.
+__device__ __forceinline__ void slice3(float2 v, float scale, uint32_t &w1, uint32_t &w2, uint32_t &w3) {
+    const float xr = v.x * scale, xi = v.y * scale;
+    const float r1 = rintf(xr), i1 = rintf(xi);
+    const float xr2 = (xr - r1) * 512.f, xi2 = (xi - i1) * 512.f;
+    const float r2 = rintf(xr2), i2 = rintf(xi2);
+    const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
+    w1 = pack_half2(r1, i1);
+    w2 = pack_half2(r2, i2);
+    w3 = pack_half2(r3 * (1.f / 512.f), i3 * (1.f / 512.f));
+}
+
+template <int K, bool XP>
 __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
     using S = TcShape<K>;
     constexpr uint32_t D = S::D, KD = S::KD, NS = S::NS, NOUT = S::NOUT;
@@ -157,15 +194,17 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
         for (int j = 0; j < K; ++j) g = insert_zero32(g, a.lp[j]);
         return g;
     };
-    auto member_offsets = [&](uint32_t (&coff)[D]) {
+    // offset of group member c (bit j of c at tile bit lp[j]); for the unrolled constant
+    // c this is an OR of the bits 1 << lp[j] held in K registers
+    uint32_t tbit[K];
 #pragma unroll
-        for (uint32_t c = 0; c < D; ++c) {
-            uint32_t o = 0;
+    for (int j = 0; j < K; ++j) tbit[j] = 1u << a.lp[j];
+    auto member_off = [&](uint32_t c) {
+        uint32_t o = 0;
 #pragma unroll
-            for (int j = 0; j < K; ++j)
-                if ((c >> j) & 1) o |= 1u << a.lp[j];
-            coff[c] = o;
-        }
+        for (int j = 0; j < K; ++j)
+            if ((c >> j) & 1u) o |= tbit[j];
+        return o;
     };
 
     if (warp == 4) {
@@ -223,20 +262,24 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
     } else if (warp < 4) {
         // ------------------------------------------------------------ transform
         const uint32_t row = tid;
-        uint32_t coff[D];
-        member_offsets(coff);
         const uint32_t gbase = group_base(row);
+        const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
+        uint32_t cx = 0;
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if ((xl >> q) & 1u) cx |= tbit[q];
         uint32_t j = 0;
         for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
             const uint32_t s = j % NS;
             bool ok = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
             if (!named_bar_and(1, 128, ok)) break;
             const float2 *rs = reinterpret_cast<const float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
+            // the row, members in the lane's order c ^ x, and its largest component
             float2 v[D];
             float m = 0.f;
 #pragma unroll
             for (uint32_t c = 0; c < D; ++c) {
-                v[c] = rs[gbase | coff[c]];
+                v[c] = rs[gbase | (XP ? (member_off(c) ^ cx) : member_off(c))];
                 m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
             }
             fence_proxy_async_smem();             // reads of the raw stage before its refill
@@ -253,28 +296,40 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             // slot j & 3 was last read by the epilogue of tile j - 4, which finished before
             // the MMAs of tile j - 2 were issued, whose completion released a_empty[ab]
             row_scale[j & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
-            // three 9-bit integer slices, one FP16 pair (re, im) per 32-bit TMEM column
-            uint32_t w1[D], w2[D], w3[D];
-#pragma unroll
-            for (uint32_t c = 0; c < D; ++c) {
-                const float xr = v[c].x * scale, xi = v[c].y * scale;
-                const float r1 = rintf(xr), i1 = rintf(xi);
-                const float xr2 = (xr - r1) * 512.f, xi2 = (xi - i1) * 512.f;
-                const float r2 = rintf(xr2), i2 = rintf(xi2);
-                const float r3 = rintf((xr2 - r2) * 512.f), i3 = rintf((xi2 - i2) * 512.f);
-                w1[c] = pack_half2(r1, i1);
-                w2[c] = pack_half2(r2, i2);
-                w3[c] = pack_half2(r3 * (1.f / 512.f), i3 * (1.f / 512.f));   // A3 2^-9, exact
-            }
             const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + ((warp * 32u) << 16);
-            if constexpr (D == 32) {
-                tmem_st32(arow, w1);
-                tmem_st32(arow + S::A_COLS, w2);
-                tmem_st32(arow + 2 * S::A_COLS, w3);
+            if constexpr (XP) {
+                // sixteen members at a time: back in member order (x < 16), three 9-bit
+                // integer slices, one FP16 pair (re, im) per 32-bit TMEM column, stored eight
+                // members at a time
+#pragma unroll
+                for (uint32_t b0 = 0; b0 < D; b0 += 16) {
+                    float2 (&vb)[16] = *reinterpret_cast<float2 (*)[16]>(&v[b0]);
+                    xor_unpermute(vb, xl, a.xt);
+#pragma unroll
+                    for (uint32_t c0 = 0; c0 < 16; c0 += 8) {
+                        uint32_t w1[8], w2[8], w3[8];
+#pragma unroll
+                        for (uint32_t c = 0; c < 8; ++c) slice3(vb[c0 + c], scale, w1[c], w2[c], w3[c]);
+                        tmem_st8_async(arow + b0 + c0, w1);
+                        tmem_st8_async(arow + S::A_COLS + b0 + c0, w2);
+                        tmem_st8_async(arow + 2 * S::A_COLS + b0 + c0, w3);
+                    }
+                }
+                tmem_wait_st();
             } else {
-                tmem_st16(arow, w1);
-                tmem_st16(arow + S::A_COLS, w2);
-                tmem_st16(arow + 2 * S::A_COLS, w3);
+                // three 9-bit integer slices, one FP16 pair (re, im) per 32-bit TMEM column
+                uint32_t w1[D], w2[D], w3[D];
+#pragma unroll
+                for (uint32_t c = 0; c < D; ++c) slice3(v[c], scale, w1[c], w2[c], w3[c]);
+                if constexpr (D == 32) {
+                    tmem_st32(arow, w1);
+                    tmem_st32(arow + S::A_COLS, w2);
+                    tmem_st32(arow + 2 * S::A_COLS, w3);
+                } else {
+                    tmem_st16(arow, w1);
+                    tmem_st16(arow + S::A_COLS, w2);
+                    tmem_st16(arow + 2 * S::A_COLS, w3);
+                }
             }
             tc_fence_before();
             named_bar(1, 128);
@@ -288,9 +343,12 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
         const uint32_t quad = warp & 3u;          // TMEM lanes 32*quad .. 32*quad+31
         const uint32_t row = quad * 32u + lane;
         const uint32_t et = tid - 192u;           // 0..127 within the epilogue warps
-        uint32_t coff[D];
-        member_offsets(coff);
         const uint32_t gbase = group_base(row);
+        const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
+        uint32_t cx = 0;
+#pragma unroll
+        for (int q = 0; q < K; ++q)
+            if ((xl >> q) & 1u) cx |= tbit[q];
         SegLanes sl;                              // the first epilogue warp stores segments
         sl.init(a.L, a.h, a.hi, lane);
         uint32_t j = 0;
@@ -310,11 +368,24 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
                 float d0[32], d12[32];
                 tmem_ld32(lane_addr + c0, d0);
                 tmem_ld32(lane_addr + KD + c0, d12);
+                if constexpr (XP) {
+                    float2 o[16];
 #pragma unroll
-                for (uint32_t i = 0; i < 32; i += 2) {
-                    const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
-                    const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
-                    out[gbase | coff[(c0 + i) / 2]] = make_float2(re, im);
+                    for (uint32_t i = 0; i < 32; i += 2) {
+                        const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
+                        const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
+                        o[i / 2] = make_float2(re, im);
+                    }
+                    xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < 16)
+#pragma unroll
+                    for (uint32_t c = 0; c < 16; ++c) out[gbase | (member_off(c0 / 2 + c) ^ cx)] = o[c];
+                } else {
+#pragma unroll
+                    for (uint32_t i = 0; i < 32; i += 2) {
+                        const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
+                        const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
+                        out[gbase | member_off((c0 + i) / 2)] = make_float2(re, im);
+                    }
                 }
             }
             tc_fence_before();
@@ -344,8 +415,11 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     static std::once_flag once;
     static cudaError_t init_err = cudaSuccess;
     std::call_once(once, [] {
-        init_err = cudaFuncSetAttribute(apply_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        init_err = cudaFuncSetAttribute(apply_tc<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)S::SMEM);
+        if (init_err == cudaSuccess)
+            init_err = cudaFuncSetAttribute(apply_tc<K, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     });
     if (init_err != cudaSuccess)
         return svi::set_error(SV_ERR_CUDA, std::string("tensor-core kernel setup: ") +
@@ -381,8 +455,15 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     a.h = p.h;
     for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
     for (int j = 0; j < K; ++j) a.lp[j] = p.lp[j];
+    // 8-byte accesses: bank pair = tile bits 0..3; targets there get lane-dependent order
+    a.xt = 0;
+    while (a.xt < (uint32_t)K && p.lp[a.xt] < 4u) ++a.xt;
+    a.xs = 4u - a.xt;
     const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
-    apply_tc<K><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    // the permutation pays off from three targets in bits 0..3 (8-way conflicts and worse);
+    // with one or two the 2- and 4-way conflicts cost less than the permutation
+    if (a.xt >= 3) apply_tc<K, true><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    else apply_tc<K, false><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }
@@ -396,8 +477,12 @@ bool tc_eligible(const sv_state *s, const Gate &g) {
            !(s->policy & SV_POLICY_NO_TENSOR_CORES);
 }
 
+// Width-4 gates run as width-5 ones (U (x) I) where the state allows: the k = 5 kernel
+// moves a tile with half the per-tile overhead of the k = 4 one for the same bytes.
 sv_status launch_apply_tc(sv_state *s, const Gate &g) {
-    return g.k == 5 ? svk::launch_tc_t<5>(s, g) : svk::launch_tc_t<4>(s, g);
+    if (g.k == 5) return svk::launch_tc_t<5>(s, g);
+    if (s->n >= svk::TcShape<5>::TB) return svk::launch_tc_t<5>(s, widen_gate(g, s->n, 5));
+    return svk::launch_tc_t<4>(s, g);
 }
 
 }  // namespace svi

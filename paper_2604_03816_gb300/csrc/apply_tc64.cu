@@ -77,7 +77,37 @@ struct Tc64Args {
     uint32_t L, h;
     uint32_t hi[SV_MAX_K];
     uint32_t lp[4];
+    // bank-conflict avoidance: the xt (<= 2) lowest targets sit at tile bits below 3; lane
+    // l takes the members of each group of four in the order c ^ x(l), x(l) = (l >> xs) &
+    // (2^xt - 1)
+    uint32_t xs, xt;
 };
+
+// v[c] <- v[c ^ x] for c < 4 and the low xt (<= 2) bits of x.
+template <typename T, typename Sel>
+__device__ __forceinline__ void xor_unpermute4(T (&v)[4], uint32_t x, uint32_t xt, Sel sel) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (xt > (uint32_t)j) {                       // uniform over the launch
+            const bool f = (x >> j) & 1u;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c & (1 << j)) continue;
+                const T lo = v[c], hi = v[c | (1 << j)];
+                v[c] = sel(f, hi, lo);
+                v[c | (1 << j)] = sel(f, lo, hi);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint4 sel_u4(bool f, uint4 a, uint4 b) {
+    return make_uint4(f ? a.x : b.x, f ? a.y : b.y, f ? a.z : b.z, f ? a.w : b.w);
+}
+
+__device__ __forceinline__ double2 sel_d2(bool f, double2 a, double2 b) {
+    return make_double2(f ? a.x : b.x, f ? a.y : b.y);
+}
 
 // Digit-pair word -> FP16 pair of digits: the patterns read 2048 + 2u, and
 // (2048 + 2u) 0.5 - 1280 = u - 256 is exact in one half2 multiply-add.
@@ -95,6 +125,9 @@ __device__ __forceinline__ double combine_levels(float f0, float f1, float f2, f
                               __float2int_rn(f2), __float2int_rn(f3), __float2int_rn(f45 * 16.f), p);
 }
 
+// XP: the launch has targets among tile bits 0..2 and takes members in the lane's XOR
+// order; otherwise no permutation code at all.
+template <bool XP>
 __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc64Args a) {
     using S = Tc64;
     constexpr uint32_t KD = S::KD, NS = S::NS, NOUT = S::NOUT;
@@ -230,6 +263,8 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         const uint32_t part = warp >> 2;
         const uint32_t gbase = group_base(row);
         const uint32_t lo_off[4] = {0u, 1u << a.lp[0], 1u << a.lp[1], (1u << a.lp[0]) | (1u << a.lp[1])};
+        const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
+        const uint32_t cx = ((xl & 1u) << a.lp[0]) | (((xl >> 1) & 1u) << a.lp[1]);
         uint32_t j = 0;
         for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
             const uint32_t s = j % NS;
@@ -241,7 +276,8 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
             uint32_t em = 0;                      // largest |high word|: its exponent field
 #pragma unroll
             for (uint32_t c = 0; c < 8; ++c) {
-                const uint32_t *w = reinterpret_cast<const uint32_t *>(rs + (gbase | member_off(part * 8u + c)));
+                const uint32_t *w = reinterpret_cast<const uint32_t *>(
+                    rs + (gbase | (XP ? (member_off(part * 8u + c) ^ cx) : member_off(part * 8u + c))));
                 em = max(em, max(w[1] & 0x7FFFFFFFu, w[3] & 0x7FFFFFFFu));
             }
             emax_part[part][row] = max(em >> 20, 1u);
@@ -254,9 +290,14 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
             for (uint32_t c0 = part * 8u; c0 < part * 8u + 8u; c0 += 4) {
                 const uint32_t hoff = gbase | (((c0 >> 2) & 1u) << a.lp[2]) | (((c0 >> 3) & 1u) << a.lp[3]);
                 uint32_t w[6][4];
+                uint4 va[4];
+#pragma unroll
+                for (uint32_t c = 0; c < 4; ++c)
+                    va[c] = *reinterpret_cast<const uint4 *>(rs + (hoff | (XP ? (lo_off[c] ^ cx) : lo_off[c])));
+                if constexpr (XP) xor_unpermute4(va, xl, a.xt, sel_u4);
 #pragma unroll
                 for (uint32_t c = 0; c < 4; ++c) {
-                    const uint4 v = *reinterpret_cast<const uint4 *>(rs + (hoff | lo_off[c]));
+                    const uint4 v = va[c];
                     uint32_t rh, rl, ih, il, t[6];
                     fxp::offset_fixed(v.y, v.x, emax, rh, rl);
                     fxp::offset_fixed(v.w, v.z, emax, ih, il);
@@ -286,6 +327,8 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         const uint32_t part = et >> 7;
         const uint32_t gbase = group_base(row);
         const uint32_t lo_off[4] = {0u, 1u << a.lp[0], 1u << a.lp[1], (1u << a.lp[0]) | (1u << a.lp[1])};
+        const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
+        const uint32_t cx = ((xl & 1u) << a.lp[0]) | (((xl >> 1) & 1u) << a.lp[1]);
         SegLanes sl;
         sl.init(a.L, a.h, a.hi, lane);
         uint32_t j = 0;
@@ -307,14 +350,18 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
                 tmem_ld8x5(lane_addr + c0, KD, d);
                 const uint32_t m0 = c0 >> 1;
                 const uint32_t hoff = gbase | (((m0 >> 2) & 1u) << a.lp[2]) | (((m0 >> 3) & 1u) << a.lp[3]);
+                double2 o[4];
 #pragma unroll
                 for (uint32_t c = 0; c < 4; ++c) {
                     const double re = combine_levels(d[0][2 * c], d[1][2 * c], d[2][2 * c],
                                                      d[3][2 * c], d[4][2 * c], p);
                     const double im = combine_levels(d[0][2 * c + 1], d[1][2 * c + 1], d[2][2 * c + 1],
                                                      d[3][2 * c + 1], d[4][2 * c + 1], p);
-                    out[hoff | lo_off[c]] = make_double2(re, im);
+                    o[c] = make_double2(re, im);
                 }
+                if constexpr (XP) xor_unpermute4(o, xl, a.xt, sel_d2);   // o[c] = member c ^ x
+#pragma unroll
+                for (uint32_t c = 0; c < 4; ++c) out[hoff | (XP ? (lo_off[c] ^ cx) : lo_off[c])] = o[c];
             }
             tc_fence_before();
             fence_proxy_async_smem();
@@ -336,56 +383,16 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
     if (warp == S::W_MMA) tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
-// U (x) I: gate g embedded on the sorted qubit set qs (m qubits, a superset of g's).
-svi::Gate widen(const svi::Gate &g, const uint32_t *qs, uint32_t m) {
-    int pos[SV_MAX_K];
-    uint32_t amask = 0;
-    for (uint32_t j = 0; j < g.k; ++j) {
-        uint32_t p = 0;
-        while (qs[p] != g.t[j]) ++p;
-        pos[j] = (int)p;
-        amask |= 1u << p;
-    }
-    svi::Gate w;
-    w.k = m;
-    for (uint32_t j = 0; j < m; ++j) w.t[j] = qs[j];
-    const int d = 1 << m, dg = 1 << g.k;
-    w.u.assign((size_t)d * d, svi::cplx(0.0, 0.0));
-    for (int r = 0; r < d; ++r)
-        for (int c = 0; c < d; ++c) {
-            if ((r & ~amask) != (c & ~amask)) continue;
-            int er = 0, ec = 0;
-            for (uint32_t j = 0; j < g.k; ++j) {
-                er |= ((r >> pos[j]) & 1) << j;
-                ec |= ((c >> pos[j]) & 1) << j;
-            }
-            w.u[(size_t)r * d + c] = g.u[(size_t)er * dg + ec];
-        }
-    return w;
-}
-
-// Four sorted targets: g's own plus the smallest other qubits at or above bit 5 (below
-// it only if the state is too small).
-void widen_targets(const svi::Gate &g, uint32_t n, uint32_t *qs) {
-    bool used[64] = {false};
-    for (uint32_t j = 0; j < g.k; ++j) used[g.t[j]] = true;
-    uint32_t m = g.k;
-    for (uint32_t q = 5; q < n && m < 4; ++q)
-        if (!used[q]) { used[q] = true; ++m; }
-    for (uint32_t q = 0; q < n && m < 4; ++q)
-        if (!used[q]) { used[q] = true; ++m; }
-    uint32_t i = 0;
-    for (uint32_t q = 0; q < n && i < 4; ++q)
-        if (used[q]) qs[i++] = q;
-}
-
 sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
     using S = Tc64;
     static std::once_flag once;
     static cudaError_t init_err = cudaSuccess;
     std::call_once(once, [] {
-        init_err = cudaFuncSetAttribute(apply_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        init_err = cudaFuncSetAttribute(apply_tc64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)S::SMEM);
+        if (init_err == cudaSuccess)
+            init_err = cudaFuncSetAttribute(apply_tc64<true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     });
     if (init_err != cudaSuccess)
         return svi::set_error(SV_ERR_CUDA, std::string("tensor-core kernel setup: ") +
@@ -393,9 +400,7 @@ sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
     svi::Gate gw;
     const svi::Gate *g = &g0;
     if (g0.k < 4) {
-        uint32_t qs[4];
-        widen_targets(g0, s->n, qs);
-        gw = widen(g0, qs, 4);
+        gw = svi::widen_gate(g0, s->n, 4);
         g = &gw;
     }
     const Plan p = make_plan(s->n, 4, g->t, S::TB);
@@ -423,8 +428,16 @@ sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
     a.h = p.h;
     for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
     for (int j = 0; j < 4; ++j) a.lp[j] = p.lp[j];
+    // 16-byte accesses: bank group = tile bits 0..2; the lowest targets there (at most
+    // two, the ones inside a group of four members) get a lane-dependent order
+    uint32_t tl = 0;
+    while (tl < 3u && p.lp[tl] < 3u) ++tl;
+    a.xs = 3u - tl;
+    a.xt = std::min(tl, 2u);
     const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
-    apply_tc64<<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    // the permutation pays off from two targets in bits 0..2 (4-way conflicts and worse)
+    if (a.xt >= 2) apply_tc64<true><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    else apply_tc64<false><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }

@@ -191,6 +191,28 @@ std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t m
     return out;
 }
 
+// g widened to m qubits: U (x) I on extra qubits, the smallest non-targets at or above
+// bit 5 (below it only if the state is too small), so that the kernels' rows stay
+// contiguous in shared memory.
+Gate widen_gate(const Gate &g, uint32_t n, uint32_t m) {
+    bool used[64] = {false};
+    for (uint32_t j = 0; j < g.k; ++j) used[g.t[j]] = true;
+    uint32_t k = g.k;
+    for (uint32_t q = 5; q < n && k < m; ++q)
+        if (!used[q]) { used[q] = true; ++k; }
+    for (uint32_t q = 0; q < n && k < m; ++q)
+        if (!used[q]) { used[q] = true; ++k; }
+    uint32_t qs[SV_MAX_K];
+    uint32_t i = 0;
+    for (uint32_t q = 0; q < n && i < m; ++q)
+        if (used[q]) qs[i++] = q;
+    Gate w;
+    w.k = m;
+    for (uint32_t j = 0; j < m; ++j) w.t[j] = qs[j];
+    w.u = embed(g, qs, m);
+    return w;
+}
+
 // Replay a recorded plan on gates with the same qubit sets: Algorithm 2's decisions
 // depend only on the qubits, so this yields the schedule fuse_gates would produce, with
 // the same products computed in the same order.

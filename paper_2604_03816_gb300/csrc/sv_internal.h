@@ -38,6 +38,8 @@ struct FusePlan {
 // Algorithm 2 over sorted gates (fuse.cpp); records its decisions in *plan if given.
 std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k,
                              FusePlan *plan = nullptr);
+// g as an m-qubit gate U (x) I (m >= g.k, m <= n; fuse.cpp).
+Gate widen_gate(const Gate &g, uint32_t n, uint32_t m);
 // Apply a recorded plan to gates with the same qubit sets (fuse.cpp).
 std::vector<Gate> replay_fusion(std::vector<Gate> nodes, const FusePlan &plan);
 
