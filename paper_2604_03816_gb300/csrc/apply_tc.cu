@@ -25,16 +25,21 @@
 // below 2^-27 of the row's largest amplitude).
 //
 // One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
-//   warp 4 (one thread)  TMA producer: 1-D bulk loads of each tile's 2^h segments into a
-//                        ring of NS raw stages;
-//   warps 0-3            transform: one group (row of A) per thread -- gather from the
-//                        raw stage, cut into three 9-bit slices and write them into
-//                        tensor memory with tcgen05.st (the thread's own TMEM lane);
-//   warp 5 (one thread)  MMA issuer: 6 x K/16 tcgen05.mma.kind::f16, A from TMEM and B
-//                        from shared memory, into three TMEM accumulators
+//   warp 8               TMA producer: lane i issues the 1-D bulk load of segment i of
+//                        each tile into a ring of NS raw stages;
+//   warps 0-7            transform: two warps per TMEM lane quadrant, one group (row of A)
+//                        and half of its members per thread -- gather from the raw stage,
+//                        cut into three 9-bit slices and write them into tensor memory
+//                        with tcgen05.st (the thread's own TMEM lane);
+//   warp 9 (one thread)  MMA issuer: 6 x K/16 tcgen05.mma.kind::f16, A from TMEM and B
+//                        from shared memory, into two TMEM accumulators
 //                        (double-buffered), committed to mbarriers;
-//   warps 6-9            epilogue: tcgen05.ld of their 32-lane quadrant, combine, scatter
-//                        into an output staging tile, TMA bulk stores.
+//   warps 10-17          epilogue: two warps per quadrant, tcgen05.ld of half the columns,
+//                        combine, scatter into an output staging tile; warp 10 issues the
+//                        TMA bulk stores.
+// Launches with targets among tile bits 0..3 (where 8-byte accesses pick their bank) take
+// each group's members in a lane-dependent XOR order, undone in registers, so that the
+// lanes of a warp hit different banks.
 // So loads, slicing, MMAs and stores of consecutive tiles overlap.  With A in tensor
 // memory, shared memory holds only B, the raw stages and the output staging, so 4 (k = 5)
 // or 8 (k = 4) tiles of loads can be in flight per SM.  Every wait is bounded and any
@@ -75,7 +80,10 @@ struct TcShape {
     static constexpr uint32_t OFF_RAW = NB * B_BYTES;
     static constexpr uint32_t OFF_OUT = OFF_RAW + NS * TILE_BYTES;
     static constexpr uint32_t SMEM = OFF_OUT + NOUT * TILE_BYTES;
-    static constexpr uint32_t THREADS = 320;              // 10 warps
+    static constexpr uint32_t THREADS = 576;              // 18 warps
+    // warps 0-7 transform, 8 TMA producer, 9 MMA issuer, 10-17 epilogue
+    static constexpr uint32_t W_PROD = 8, W_MMA = 9, W_EPI = 10;
+    static constexpr uint32_t HALF = D / 2;               // group members per worker thread
 };
 
 template <int K>
@@ -117,8 +125,6 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// XP: the launch has targets among tile bits 0..3 and takes members in the lane's XOR
-// order; otherwise every lane takes them in member order (no permutation code at all).
 // Three 9-bit integer slices of a scaled amplitude (|x scale| < 256): FP16 pairs
 // (re, im) of a1, a2 and a3 2^-9, all exact.
 __device__ __forceinline__ void slice3(float2 v, float scale, uint32_t &w1, uint32_t &w2, uint32_t &w3) {
@@ -132,15 +138,18 @@ __device__ __forceinline__ void slice3(float2 v, float scale, uint32_t &w1, uint
     w3 = pack_half2(r3 * (1.f / 512.f), i3 * (1.f / 512.f));
 }
 
+// XP: the launch has targets among tile bits 0..3 and takes members in the lane's XOR
+// order; otherwise every lane takes them in member order (no permutation code at all).
 template <int K, bool XP>
-__global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
+__global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
     using S = TcShape<K>;
-    constexpr uint32_t D = S::D, KD = S::KD, NS = S::NS, NOUT = S::NOUT;
+    constexpr uint32_t KD = S::KD, NS = S::NS, NOUT = S::NOUT, HALF = S::HALF;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
     __shared__ __align__(8) unsigned long long a_full[2], a_empty[2], d_full[2], d_empty[2];
     __shared__ __align__(8) unsigned long long scale_full[4];   // row scales, tile j -> j & 3
     __shared__ float row_scale[4][128];
+    __shared__ float max_part[2][128];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     // B slices, the raw stages and the output staging tiles; B operand reads stay inside
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
     const uint32_t seg_bytes = seg_amps * 8u;
     const uint32_t nseg = 1u << a.h;
 
-    if (warp == 5) {
+    if (warp == S::W_MMA) {
         tmem_alloc(smem_u32(&tmem_slot), S::TMEM_COLS);
         tmem_relinquish();
     }
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
         return o;
     };
 
-    if (warp == 4) {
+    if (warp == S::W_PROD) {
         // ------------------------------------------------------------ TMA producer
         // lane i issues the bulk copy of segment i of every tile
         SegLanes sl;
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
                          seg_bytes, bar);
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == S::W_MMA) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(S::ROWS, KD);
@@ -259,9 +268,12 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
                 mma_commit(smem_u32(&d_full[b]));
             }
         }
-    } else if (warp < 4) {
+    } else if (warp < S::W_PROD) {
         // ------------------------------------------------------------ transform
-        const uint32_t row = tid;
+        // Two warps per TMEM lane quadrant: warp w takes rows 32 (w & 3) .. + 31 and group
+        // members HALF (w >> 2) .. + HALF - 1.
+        const uint32_t row = (warp & 3u) * 32u + lane;
+        const uint32_t part = warp >> 2;
         const uint32_t gbase = group_base(row);
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         uint32_t cx = 0;
@@ -272,77 +284,61 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
         for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
             const uint32_t s = j % NS;
             bool ok = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
-            if (!named_bar_and(1, 128, ok)) break;
             const float2 *rs = reinterpret_cast<const float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
-            // the row, members in the lane's order c ^ x, and its largest component
-            float2 v[D];
+            // this half of the row (members in the lane's order c ^ x) and its largest component
+            float2 v[HALF];
             float m = 0.f;
 #pragma unroll
-            for (uint32_t c = 0; c < D; ++c) {
-                v[c] = rs[gbase | (XP ? (member_off(c) ^ cx) : member_off(c))];
+            for (uint32_t c = 0; c < HALF; ++c) {
+                const uint32_t mo = member_off(part * HALF + c);
+                v[c] = rs[gbase | (XP ? (mo ^ cx) : mo)];
                 m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
             }
+            max_part[part][row] = m;
             fence_proxy_async_smem();             // reads of the raw stage before its refill
-            named_bar(1, 128);
-            if (row == 0) mbar_arrive(smem_u32(&empty[s]));
+            if (!named_bar_and(1, 256, ok)) break;
+            if (tid == 0) mbar_arrive(smem_u32(&empty[s]));
+            m = fmaxf(max_part[0][row], max_part[1][row]);
             int ex = 0;
             frexpf(m, &ex);                       // m < 2^ex (m = 0: ex = 0)
             ex = max(ex, -100);                   // keep 2^(8-ex) finite
             const float scale = ldexpf(1.f, 8 - ex);   // |x * scale| < 256
             const uint32_t ab = j & 1u;
             ok = mbar_wait_or_abort(smem_u32(&a_empty[ab]), ((j >> 1) & 1u) ^ 1u, abort);
-            if (!named_bar_and(1, 128, ok)) break;
+            if (!named_bar_and(1, 256, ok)) break;
             tc_fence_after();
             // slot j & 3 was last read by the epilogue of tile j - 4, which finished before
             // the MMAs of tile j - 2 were issued, whose completion released a_empty[ab]
-            row_scale[j & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
-            const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + ((warp * 32u) << 16);
-            if constexpr (XP) {
-                // sixteen members at a time: back in member order (x < 16), three 9-bit
-                // integer slices, one FP16 pair (re, im) per 32-bit TMEM column, stored eight
-                // members at a time
+            if (part == 0) row_scale[j & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
+            if constexpr (XP) xor_unpermute(v, xl, a.xt);   // back in member order (x < HALF)
+            // three 9-bit integer slices, one FP16 pair (re, im) per 32-bit TMEM column,
+            // stored eight members at a time
+            const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + (((warp & 3u) * 32u) << 16) +
+                                  part * HALF;
 #pragma unroll
-                for (uint32_t b0 = 0; b0 < D; b0 += 16) {
-                    float2 (&vb)[16] = *reinterpret_cast<float2 (*)[16]>(&v[b0]);
-                    xor_unpermute(vb, xl, a.xt);
+            for (uint32_t c0 = 0; c0 < HALF; c0 += 8) {
+                uint32_t w1[8], w2[8], w3[8];
 #pragma unroll
-                    for (uint32_t c0 = 0; c0 < 16; c0 += 8) {
-                        uint32_t w1[8], w2[8], w3[8];
-#pragma unroll
-                        for (uint32_t c = 0; c < 8; ++c) slice3(vb[c0 + c], scale, w1[c], w2[c], w3[c]);
-                        tmem_st8_async(arow + b0 + c0, w1);
-                        tmem_st8_async(arow + S::A_COLS + b0 + c0, w2);
-                        tmem_st8_async(arow + 2 * S::A_COLS + b0 + c0, w3);
-                    }
-                }
-                tmem_wait_st();
-            } else {
-                // three 9-bit integer slices, one FP16 pair (re, im) per 32-bit TMEM column
-                uint32_t w1[D], w2[D], w3[D];
-#pragma unroll
-                for (uint32_t c = 0; c < D; ++c) slice3(v[c], scale, w1[c], w2[c], w3[c]);
-                if constexpr (D == 32) {
-                    tmem_st32(arow, w1);
-                    tmem_st32(arow + S::A_COLS, w2);
-                    tmem_st32(arow + 2 * S::A_COLS, w3);
-                } else {
-                    tmem_st16(arow, w1);
-                    tmem_st16(arow + S::A_COLS, w2);
-                    tmem_st16(arow + 2 * S::A_COLS, w3);
-                }
+                for (uint32_t c = 0; c < 8; ++c) slice3(v[c0 + c], scale, w1[c], w2[c], w3[c]);
+                tmem_st8_async(arow + c0, w1);
+                tmem_st8_async(arow + S::A_COLS + c0, w2);
+                tmem_st8_async(arow + 2 * S::A_COLS + c0, w3);
             }
+            tmem_wait_st();
             tc_fence_before();
-            named_bar(1, 128);
-            if (row == 0) {
+            named_bar(1, 256);                    // also: max_part is free for the next tile
+            if (tid == 0) {
                 mbar_arrive(smem_u32(&a_full[ab]));
                 mbar_arrive(smem_u32(&scale_full[j & 3u]));
             }
         }
-    } else {
+    } else if (warp >= S::W_EPI) {
         // ------------------------------------------------------------ epilogue
+        // Two warps per lane quadrant, each over half of the accumulator columns.
         const uint32_t quad = warp & 3u;          // TMEM lanes 32*quad .. 32*quad+31
         const uint32_t row = quad * 32u + lane;
-        const uint32_t et = tid - 192u;           // 0..127 within the epilogue warps
+        const uint32_t et = tid - S::W_EPI * 32u; // 0..255 within the epilogue warps
+        const uint32_t part = et >> 7;
         const uint32_t gbase = group_base(row);
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         uint32_t cx = 0;
@@ -356,41 +352,35 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
             const uint32_t b = j & 1u, ob = j % NOUT;
             bool ok = mbar_wait_or_abort(smem_u32(&d_full[b]), (j >> 1) & 1u, abort);
             ok = ok && mbar_wait_or_abort(smem_u32(&scale_full[j & 3u]), (j >> 2) & 1u, abort);
-            if (!named_bar_and(2, 128, ok)) break;
+            if (!named_bar_and(2, 256, ok)) break;
             tc_fence_after();
             if (et < 32) bulk_wait_read<(int)NOUT - 1>();   // this staging tile is free
-            named_bar(2, 128);
+            named_bar(2, 256);
             const float osc = row_scale[j & 3u][row];
             float2 *out = reinterpret_cast<float2 *>(smem + S::OFF_OUT + ob * S::TILE_BYTES);
-            const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16);
+            const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16) + part * HALF * 2u;
+            float2 o[HALF];
 #pragma unroll
-            for (uint32_t c0 = 0; c0 < KD; c0 += 32) {
-                float d0[32], d12[32];
-                tmem_ld32(lane_addr + c0, d0);
-                tmem_ld32(lane_addr + KD + c0, d12);
-                if constexpr (XP) {
-                    float2 o[16];
+            for (uint32_t c0 = 0; c0 < 2u * HALF; c0 += 16) {
+                float d0[16], d12[16];
+                tmem_ld16(lane_addr + c0, d0);
+                tmem_ld16(lane_addr + KD + c0, d12);
 #pragma unroll
-                    for (uint32_t i = 0; i < 32; i += 2) {
-                        const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
-                        const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
-                        o[i / 2] = make_float2(re, im);
-                    }
-                    xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < 16)
-#pragma unroll
-                    for (uint32_t c = 0; c < 16; ++c) out[gbase | (member_off(c0 / 2 + c) ^ cx)] = o[c];
-                } else {
-#pragma unroll
-                    for (uint32_t i = 0; i < 32; i += 2) {
-                        const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
-                        const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
-                        out[gbase | member_off((c0 + i) / 2)] = make_float2(re, im);
-                    }
+                for (uint32_t i = 0; i < 16; i += 2) {
+                    const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
+                    const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
+                    o[(c0 + i) / 2] = make_float2(re, im);
                 }
+            }
+            if constexpr (XP) xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < HALF)
+#pragma unroll
+            for (uint32_t c = 0; c < HALF; ++c) {
+                const uint32_t mo = member_off(part * HALF + c);
+                out[gbase | (XP ? (mo ^ cx) : mo)] = o[c];
             }
             tc_fence_before();
             fence_proxy_async_smem();
-            named_bar(2, 128);
+            named_bar(2, 256);
             if (et == 0) mbar_arrive(smem_u32(&d_empty[b]));
             if (et < 32) {
                 if (lane < nseg)
@@ -405,7 +395,7 @@ __global__ void __launch_bounds__(320, 1) apply_tc(const __grid_constant__ TcArg
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 5) tmem_dealloc(tmem, S::TMEM_COLS);
+    if (warp == S::W_MMA) tmem_dealloc(tmem, S::TMEM_COLS);
 }
 
 template <int K>
@@ -456,13 +446,13 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
     for (int j = 0; j < K; ++j) a.lp[j] = p.lp[j];
     // 8-byte accesses: bank pair = tile bits 0..3; targets there get lane-dependent order
-    a.xt = 0;
-    while (a.xt < (uint32_t)K && p.lp[a.xt] < 4u) ++a.xt;
-    a.xs = 4u - a.xt;
+    uint32_t tl = 0;
+    while (tl < (uint32_t)K && p.lp[tl] < 4u) ++tl;
+    a.xs = 4u - tl;
+    a.xt = std::min(tl, (uint32_t)K - 1u);   // permute within a worker's half of the members
     const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
-    // the permutation pays off from three targets in bits 0..3 (8-way conflicts and worse);
-    // with one or two the 2- and 4-way conflicts cost less than the permutation
-    if (a.xt >= 3) apply_tc<K, true><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    // with eight worker warps per role the permutation costs less than even 2-way conflicts
+    if (a.xt >= 1) apply_tc<K, true><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     else apply_tc<K, false><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
