@@ -35,10 +35,27 @@ METRIC = ("fused-gate HBM GB/s & circuits/s at 28–33q vs unfused c128; "
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic of one tensor-core pass (apply_tc<5>) from the ncu capture summarised in
-# profiles/apply_tc5_c64_27q_ncu.md (2.087 GB at 27 qubits), scaled by 2^3 to the 30-qubit
-# launch; valid only while the kernel sources hash to this prefix (null otherwise).
-TRAFFIC = {"sha256_prefix": "f617682c54ae1bd9", "bytes_per_launch": 2.0865e9 * 8, "n": 30}
+# DRAM traffic of one tensor-core pass from the ncu captures summarised under profiles/
+# (27-qubit launches scaled by 2^3 to the 30-qubit bench), the kernel that dominates each
+# precision's launch list, and the sources the numbers are valid for (traffic is reported
+# as null once those sources hash differently).
+KERNELS = {
+    "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
+            "sha256_prefix": "37cb841824dd087f", "n": 30,
+            "bytes_per_launch": (1.073818e9 + 1.011945e9) * 8,
+            "kernel": "fused-gate passes: apply_tc<5,*> 69.8% of GPU time, all apply kernels "
+                      "90.8% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "traffic_source": "apply_tc<5,0> ncu capture at 27q scaled to 30q "
+                              "(profiles/apply_tc5_c64_27q_ncu.md)"},
+    "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
+             "sha256_prefix": "3b3b6ab080f4a077", "n": 30,
+             "bytes_per_launch": (2.148243e9 + 2.085301e9) * 8,
+             "kernel": "fused-gate passes: apply_tc64<*> 97.9% of GPU time "
+                       "(profiles/fused_pass_grid30q_c128_k4_launches.md); bound by the "
+                       "integer ALU pipe, not HBM (profiles/apply_tc64_c128_27q_ncu.md)",
+             "traffic_source": "apply_tc64<0> ncu capture at 27q scaled to 30q "
+                               "(profiles/apply_tc64_c128_27q_ncu.md)"},
+}
 
 
 def parse():
@@ -73,9 +90,9 @@ def dist_info():
     return rank, world, local
 
 
-def kernel_sha():
+def kernel_sha(files):
     h = hashlib.sha256()
-    for f in ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2604_03816_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -426,11 +443,11 @@ def main():
         passes = sum(r["passes"] for r in reps)
         achieved = apply_bytes / (apply_ms / 1000.0) / 1e9
         peak, peak_kind = hbm_peak()
-        sha = kernel_sha()
+        kinfo = KERNELS[args.dtype]
+        sha = kernel_sha(kinfo["files"])
         traffic = None
-        if (TRAFFIC["sha256_prefix"] and sha.startswith(TRAFFIC["sha256_prefix"])
-                and args.n == TRAFFIC["n"] and args.dtype == "c64"):
-            traffic = TRAFFIC["bytes_per_launch"]
+        if sha.startswith(kinfo["sha256_prefix"]) and args.n == kinfo["n"] and args.k >= 4:
+            traffic = kinfo["bytes_per_launch"]
 
         if sv.sv_info(state)[1] != dt:          # a promotion widened the state: start over
             sv.sv_set_dtype(state, dt)
@@ -494,9 +511,8 @@ def main():
            "max_drift": max(r["drift"] for r in reps),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": traffic,
-                        "kernel": "fused-gate pass (apply_tc<5> 63% of GPU time, all apply "
-                                  "kernels 91.5%; profiles/fused_pass_grid30q_k5_launches.md)",
-                        "traffic_source": "apply_tc<5> ncu capture at 27q scaled to 30q",
+                        "kernel": kinfo["kernel"],
+                        "traffic_source": kinfo["traffic_source"],
                         "peak_kind": peak_kind,
                         "algorithmic_bytes_per_launch": apply_bytes / passes,
                         "avg_launch_ms": apply_ms / passes},
