@@ -14,6 +14,7 @@ on bounded samples of the same workload, scaled to circuits/s.
 Under torchrun each rank runs an independent replica (no collective on the data path).
 """
 import argparse
+import concurrent.futures
 import hashlib
 import json
 import os
@@ -43,8 +44,8 @@ KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
             "sha256_prefix": "37cb841824dd087f", "n": 30,
             "bytes_per_launch": (1.073818e9 + 1.011945e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,*> 69.8% of GPU time, all apply kernels "
-                      "90.8% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "kernel": "fused-gate passes: apply_tc<5,*> 74.8% of GPU time, all apply kernels "
+                      "97.5% (profiles/fused_pass_grid30q_k5_launches.md)",
             "traffic_source": "apply_tc<5,0> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
@@ -280,6 +281,8 @@ def config_dict(args, ngates, nfused):
             "n_qubits": args.n, "gates": ngates, "fused_gates": nfused, "max_k": args.k,
             "state_dtype": args.dtype, "state_bytes": (8 if args.dtype == "c64" else 16) << args.n,
             "l2": "state larger than L2 (inputs > 129 MB), no flush needed",
+            "host_fusion": "one sv_fuse per step, of the next circuit, on a host thread "
+                           "overlapping the current circuit's GPU work",
             "seed": W.seed_for(3, args.n)}
 
 
@@ -395,9 +398,15 @@ def main():
     ga = sv.GateArray(gates)
     state = sv.sv_alloc(args.n, dt, stream=stream)
     launches_per_step = [0]
+    # Each step fuses one circuit on the host (Algorithm 2) and runs it on the GPU; the
+    # fusion of the next circuit runs on a host thread while the GPU works on the current
+    # one (ctypes releases the GIL), as a pipelined simulator would.
+    fuser = concurrent.futures.ThreadPoolExecutor(max_workers=1)
+    next_c = [fuser.submit(sv.sv_fuse, gates, args.n, args.k)]
 
     def step(timing=False):
-        c = sv.sv_fuse(gates, args.n, args.k)
+        c = next_c[0].result()
+        next_c[0] = fuser.submit(sv.sv_fuse, gates, args.n, args.k)
         if sv.sv_info(state)[1] != dt:           # a promotion widened the state last time
             sv.sv_set_dtype(state, dt)
         sv.sv_set_basis(state, 0)

@@ -28,7 +28,8 @@ struct Node {
     std::set<int> preds, succs;   // ordered: predecessors are tried in ascending id
 };
 
-// Matrix of gate g (sorted targets) embedded on the sorted qubit set qs (size m).
+// Matrix of gate g (sorted targets) embedded on the sorted qubit set qs (size m):
+// g's matrix on its own positions, the identity on the others.
 std::vector<cplx> embed(const Gate &g, const uint32_t *qs, uint32_t m) {
     int pos[SV_MAX_K];
     uint32_t amask = 0;
@@ -39,40 +40,76 @@ std::vector<cplx> embed(const Gate &g, const uint32_t *qs, uint32_t m) {
         amask |= 1u << p;
     }
     const int d = 1 << m, dg = 1 << g.k;
+    int off[1 << SV_MAX_K];
+    for (int a = 0; a < dg; ++a) {
+        int r = 0;
+        for (uint32_t j = 0; j < g.k; ++j) r |= ((a >> j) & 1) << pos[j];
+        off[a] = r;
+    }
     std::vector<cplx> e((size_t)d * d, cplx(0.0, 0.0));
-    for (int r = 0; r < d; ++r) {
-        int er = 0;
-        for (uint32_t j = 0; j < g.k; ++j) er |= ((r >> pos[j]) & 1) << j;
-        for (int c = 0; c < d; ++c) {
-            if ((r & ~amask) != (c & ~amask)) continue;
-            int ec = 0;
-            for (uint32_t j = 0; j < g.k; ++j) ec |= ((c >> pos[j]) & 1) << j;
-            e[(size_t)r * d + c] = g.u[(size_t)er * dg + ec];
-        }
+    for (int e0 = 0; e0 < d; ++e0) {
+        if (e0 & amask) continue;                       // the other qubits' values
+        for (int ra = 0; ra < dg; ++ra)
+            for (int ca = 0; ca < dg; ++ca)
+                e[(size_t)(e0 | off[ra]) * d + (e0 | off[ca])] = g.u[(size_t)ra * dg + ca];
     }
     return e;
 }
 
-// Eq. 9: U_fused = U_v . U_u on the sorted qubit set qs (size m), u applied first.
+// Positions of g's targets within the sorted set qs, as a bit mask and per target.
+static uint32_t target_positions(const Gate &g, const uint32_t *qs, int *pos) {
+    uint32_t mask = 0;
+    for (uint32_t j = 0; j < g.k; ++j) {
+        uint32_t p = 0;
+        while (qs[p] != g.t[j]) ++p;
+        pos[j] = (int)p;
+        mask |= 1u << p;
+    }
+    return mask;
+}
+
+// Spread the bits of a (bit j of a -> bit pos[j]).
+static inline int deposit(int a, const int *pos, uint32_t k) {
+    int r = 0;
+    for (uint32_t j = 0; j < k; ++j) r |= ((a >> j) & 1) << pos[j];
+    return r;
+}
+
+// Eq. 9: U_fused = U_v . U_u on the sorted qubit set qs (size m), u applied first.  E(U_u)
+// is U_u itself when u already acts on all of qs (the common case: u absorbs a narrower
+// v); U_v is applied to each column in place of the dense product with E(U_v), entry by
+// entry in the same order (nonzero terms of row r, ascending column index).
 Gate fused_product(const Gate &gu, const Gate &gv, const uint32_t *qs, uint32_t m) {
-    const std::vector<cplx> eu = embed(gu, qs, m), ev = embed(gv, qs, m);
     const int d = 1 << m;
+    const std::vector<cplx> eu = gu.k == m ? gu.u : embed(gu, qs, m);
+    int pv[SV_MAX_K];
+    const uint32_t vmask = target_positions(gv, qs, pv);
+    const int dv = 1 << gv.k;
+    int off[1 << SV_MAX_K];
+    for (int a = 0; a < dv; ++a) off[a] = deposit(a, pv, gv.k);
     Gate f;
     f.k = m;
     for (uint32_t j = 0; j < m; ++j) f.t[j] = qs[j];
     f.u.assign((size_t)d * d, cplx(0.0, 0.0));
-    for (int r = 0; r < d; ++r)
-        for (int x = 0; x < d; ++x) {
-            const cplx a = ev[(size_t)r * d + x];
-            if (a == cplx(0.0, 0.0)) continue;
-            for (int c = 0; c < d; ++c) f.u[(size_t)r * d + c] += a * eu[(size_t)x * d + c];
+    for (int r0 = 0; r0 < d; ++r0) {
+        if (r0 & vmask) continue;                       // base rows: v's bits clear
+        for (int b = 0; b < dv; ++b) {
+            cplx *frow = &f.u[(size_t)(r0 | off[b]) * d];
+            for (int a = 0; a < dv; ++a) {
+                const cplx w = gv.u[(size_t)b * dv + a];
+                if (w == cplx(0.0, 0.0)) continue;
+                const cplx *urow = &eu[(size_t)(r0 | off[a]) * d];
+                for (int c = 0; c < d; ++c) frow[c] += w * urow[c];
+            }
         }
+    }
     return f;
 }
 
 class Dag {
   public:
-    Dag(const std::vector<Gate> &gates, uint32_t n) : nodes_(gates.size()), seen_(gates.size(), 0) {
+    Dag(const std::vector<Gate> &gates, uint32_t n)
+        : nodes_(gates.size()), seen_(gates.size(), 0), pos_(gates.size(), 0) {
         std::vector<int> last(n, -1);
         for (size_t i = 0; i < gates.size(); ++i) {
             nodes_[i].g = gates[i];
@@ -106,19 +143,30 @@ class Dag {
         return out;
     }
 
+    // Is there a path u -> ... -> v other than the edge (u, v)?  pos_ is the position of
+    // each vertex in the topological order the current sweep started from.  During the
+    // sweep a contraction keeps the absorbing vertex u at its (earlier) position and only
+    // adds edges into it from vertices placed before v, so a vertex placed after v still
+    // reaches only vertices placed after v: the search never needs to enter one.
     bool other_path(int u, int v) {
         ++stamp_;
-        std::vector<int> stack;
+        const int pv = pos_[v];
+        stack_.clear();
         for (int w : nodes_[u].succs)
-            if (w != v) { stack.push_back(w); seen_[w] = stamp_; }
-        while (!stack.empty()) {
-            const int w = stack.back();
-            stack.pop_back();
-            if (w == v) return true;
-            for (int x : nodes_[w].succs)
-                if (seen_[x] != stamp_) { seen_[x] = stamp_; stack.push_back(x); }
+            if (w != v && pos_[w] < pv) { stack_.push_back(w); seen_[w] = stamp_; }
+        while (!stack_.empty()) {
+            const int w = stack_.back();
+            stack_.pop_back();
+            for (int x : nodes_[w].succs) {
+                if (x == v) return true;
+                if (seen_[x] != stamp_ && pos_[x] < pv) { seen_[x] = stamp_; stack_.push_back(x); }
+            }
         }
         return false;
+    }
+
+    void set_positions(const std::vector<int> &order) {
+        for (size_t i = 0; i < order.size(); ++i) pos_[order[i]] = (int)i;
     }
 
     static uint32_t union_qubits(const Gate &a, const Gate &b, uint32_t *qs) {
@@ -158,6 +206,7 @@ class Dag {
 
     std::vector<Node> nodes_;
     std::vector<uint32_t> seen_;
+    std::vector<int> pos_, stack_;
     uint32_t stamp_ = 0;
 };
 
@@ -169,7 +218,9 @@ std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t m
     bool changed = max_k > 0;
     while (changed) {
         changed = false;
-        for (int v : dag.topo_order()) {
+        const std::vector<int> order = dag.topo_order();
+        dag.set_positions(order);
+        for (int v : order) {
             if (!dag.nodes_[v].alive) continue;
             const std::vector<int> preds(dag.nodes_[v].preds.begin(), dag.nodes_[v].preds.end());
             for (int u : preds) {

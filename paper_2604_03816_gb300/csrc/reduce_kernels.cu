@@ -58,15 +58,17 @@ __global__ void norm_c64(const float4 *__restrict__ v, unsigned long long nvec, 
     unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + 3 * stride < nvec; i += 4 * stride) {
         float4 a = v[i], b = v[i + stride], c = v[i + 2 * stride], d = v[i + 3 * stride];
-        float sa = prob_of(a.x, a.y) + prob_of(a.z, a.w);
-        float sb = prob_of(b.x, b.y) + prob_of(b.z, b.w);
-        float sc = prob_of(c.x, c.y) + prob_of(c.z, c.w);
-        float sd = prob_of(d.x, d.y) + prob_of(d.z, d.w);
-        acc += (double)sa + (double)sb + (double)sc + (double)sd;
+        const float sa = __fadd_rn(prob_of(a.x, a.y), prob_of(a.z, a.w));
+        const float sb = __fadd_rn(prob_of(b.x, b.y), prob_of(b.z, b.w));
+        const float sc = __fadd_rn(prob_of(c.x, c.y), prob_of(c.z, c.w));
+        const float sd = __fadd_rn(prob_of(d.x, d.y), prob_of(d.z, d.w));
+        // eight amplitudes summed pairwise in FP32, one FP64 operation per eight (the FP64
+        // pipe of this GPU runs at about 1/64 of the FP32 rate)
+        acc += (double)__fadd_rn(__fadd_rn(sa, sb), __fadd_rn(sc, sd));
     }
     for (; i < nvec; i += stride) {
         float4 a = v[i];
-        acc += (double)(prob_of(a.x, a.y) + prob_of(a.z, a.w));
+        acc += (double)__fadd_rn(prob_of(a.x, a.y), prob_of(a.z, a.w));
     }
     const double r = block_sum(acc);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -164,23 +166,93 @@ __global__ void expect_kernel(const __grid_constant__ ExpectArgs a, const void *
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
 }
 
+// complex64, up to NT terms of one X-part: per term FP32 partial sums over runs of eight
+// elements (pairs when x != 0), one FP64 step per run and term.  With s_t(k) = (-1)^{|k &
+// z_t|} and cc_t = ccr_t + i cci_t, a term contributes ccr_t sum_k s_t(k) |psi_k|^2 when
+// x = 0, and for x != 0, per pair (k, k2 = k ^ x) with bit hb of k clear and
+// c = conj(psi_k2) psi_k = re + i im:  ccr_t (s_t(k) + s_t(k2)) re - cci_t (s_t(k) - s_t(k2)) im.
+template <int NT, bool PAIRS>
+__global__ void expect_c64(const __grid_constant__ ExpectArgs a, const float2 *__restrict__ psi,
+                           double *partial) {
+    double A[NT], B[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) A[t] = B[t] = 0.0;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         i0 < a.npairs; i0 += 8 * stride) {
+        float sa[NT], sb[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) sa[t] = sb[t] = 0.f;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const unsigned long long i = i0 + r * stride;
+            if (i >= a.npairs) break;
+            if constexpr (!PAIRS) {
+                const float2 v = psi[i];
+                const float pr = prob_of(v.x, v.y);
+#pragma unroll
+                for (int t = 0; t < NT; ++t)
+                    sa[t] = __fadd_rn(sa[t], (__popcll(i & a.z[t]) & 1) ? -pr : pr);
+            } else {
+                const unsigned long long k = insert_zero64(i, (uint32_t)a.hb), k2 = k ^ a.x;
+                const float2 p = psi[k], q = psi[k2];
+                const float re = __fadd_rn(__fmul_rn(q.x, p.x), __fmul_rn(q.y, p.y));
+                const float im = __fsub_rn(__fmul_rn(q.x, p.y), __fmul_rn(q.y, p.x));
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    const bool s1 = __popcll(k & a.z[t]) & 1, s2 = __popcll(k2 & a.z[t]) & 1;
+                    if (s1 == s2) sa[t] = __fadd_rn(sa[t], s1 ? -2.f * re : 2.f * re);
+                    else sb[t] = __fadd_rn(sb[t], s1 ? -2.f * im : 2.f * im);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            A[t] += (double)sa[t];
+            B[t] += (double)sb[t];
+        }
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) acc += a.ccr[t] * A[t] - a.cci[t] * B[t];
+    const double r = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
 // ---------------------------------------------------------------- top-k
 
 // (p, idx) order: larger p first, then smaller index.
-__device__ __forceinline__ bool better(double pa, unsigned long long ia, double pb,
-                                       unsigned long long ib) {
+template <typename P>
+__device__ __forceinline__ bool better(P pa, unsigned long long ia, P pb, unsigned long long ib) {
     return pa > pb || (pa == pb && ia < ib);
 }
 
-struct TopList {   // one warp's 64 entries, two per lane, plus the current worst
-    double p0, p1;
+// Keys of the top-k lists.  complex64 probabilities are FP32 values, compared in FP32 (the
+// same decisions as on their exact FP64 widenings).  FP64 probabilities are compared as
+// their IEEE bit patterns, which order non-negative doubles like their values, in 64-bit
+// integer arithmetic: a warp-wide FP64 compare costs tens of cycles on this GPU.
+template <typename P> __device__ __forceinline__ P empty_key();
+template <> __device__ __forceinline__ float empty_key<float>() { return -1.f; }
+template <> __device__ __forceinline__ unsigned long long empty_key<unsigned long long>() { return 0ull; }
+
+__device__ __forceinline__ unsigned long long key_of(double p) {   // p >= 0
+    return (unsigned long long)__double_as_longlong(p);
+}
+__device__ __forceinline__ double value_of(unsigned long long k) { return __longlong_as_double((long long)k); }
+__device__ __forceinline__ double value_of(float k) { return (double)k; }
+
+// One warp's 64 entries, two per lane, plus the current worst.  Empty entries hold
+// (empty_key, ~0): they lose to every real entry.
+template <typename P>
+struct TopList {
+    P p0, p1;
     unsigned long long i0, i1;
-    double wp;
+    P wp;
     unsigned long long wi;
     int wl, ws;    // lane and slot of the worst entry
 
     __device__ void init() {
-        p0 = p1 = -1.0;
+        p0 = p1 = empty_key<P>();
         i0 = i1 = ~0ull;
         find_worst();
     }
@@ -188,12 +260,12 @@ struct TopList {   // one warp's 64 entries, two per lane, plus the current wors
         const int lane = threadIdx.x & 31;
         // this lane's worse entry
         bool second = better(p0, i0, p1, i1);
-        double p = second ? p1 : p0;
+        P p = second ? p1 : p0;
         unsigned long long ix = second ? i1 : i0;
         int l = lane, s = second ? 1 : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double op = __shfl_xor_sync(0xffffffffu, p, o);
+            const P op = __shfl_xor_sync(0xffffffffu, p, o);
             const unsigned long long oi = __shfl_xor_sync(0xffffffffu, ix, o);
             const int ol = __shfl_xor_sync(0xffffffffu, l, o);
             const int os = __shfl_xor_sync(0xffffffffu, s, o);
@@ -204,13 +276,13 @@ struct TopList {   // one warp's 64 entries, two per lane, plus the current wors
         wp = p; wi = ix; wl = l; ws = s;
     }
     // Offer one candidate per lane; all lanes of the warp must call.
-    __device__ void offer(double p, unsigned long long ix, bool valid) {
+    __device__ void offer(P p, unsigned long long ix, bool valid) {
         const int lane = threadIdx.x & 31;
         unsigned mask = __ballot_sync(0xffffffffu, valid && better(p, ix, wp, wi));
         while (mask) {
             const int src = __ffs(mask) - 1;
             mask &= mask - 1;
-            const double cp = __shfl_sync(0xffffffffu, p, src);
+            const P cp = __shfl_sync(0xffffffffu, p, src);
             const unsigned long long ci = __shfl_sync(0xffffffffu, ix, src);
             if (!better(cp, ci, wp, wi)) continue;     // uniform across the warp
             if (lane == wl) {
@@ -221,59 +293,125 @@ struct TopList {   // one warp's 64 entries, two per lane, plus the current wors
     }
 };
 
+// Pass 1: each warp scans a contiguous chunk (a multiple of 256 amplitudes), eight
+// amplitudes per lane per step from independent 16-byte loads; a step is offered to the
+// warp's list only if some lane holds a probability not below the list's current worst.
+// The block's warps then merge their lists, and the block writes 64 candidates.
 template <typename R>
-__global__ void topk_pass1(const void *psi_, unsigned long long N, unsigned long long chunk,
-                           double *cand_p, unsigned long long *cand_i) {
-    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
-    const C *psi = reinterpret_cast<const C *>(psi_);
-    const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) topk_pass1(const void *psi_, unsigned long long N,
+                                                  unsigned long long chunk, double *cand_p,
+                                                  unsigned long long *cand_i) {
+    using Key = typename std::conditional<sizeof(R) == 4, float, unsigned long long>::type;
+    __shared__ Key lp[8][64];
+    __shared__ unsigned long long li[8][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    TopList L;
+    TopList<Key> L;
     L.init();
     const unsigned long long lo = warp * chunk, hi = min(N, lo + chunk);
-    for (unsigned long long b = lo; b < hi; b += 32) {
-        const unsigned long long k = b + lane;
-        double p = -1.0;
-        if (k < hi) {
-            const C v = psi[k];
-            p = (double)prob_of(v.x, v.y);
+    for (unsigned long long b = lo; b < hi; b += 256) {
+        Key p[8];
+        unsigned long long k[8];
+        bool ok[8];
+        if constexpr (sizeof(R) == 4) {
+            // four float4 loads: amplitudes b + 2 (lane + 32 j) + {0, 1}
+            const float4 *v4 = reinterpret_cast<const float4 *>(psi_);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const unsigned long long k0 = b + 2ull * (lane + 32 * j);
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k0 < hi) v = v4[k0 >> 1];
+                k[2 * j] = k0;
+                k[2 * j + 1] = k0 + 1;
+                ok[2 * j] = k0 < hi;
+                ok[2 * j + 1] = k0 + 1 < hi;
+                p[2 * j] = ok[2 * j] ? prob_of(v.x, v.y) : empty_key<Key>();
+                p[2 * j + 1] = ok[2 * j + 1] ? prob_of(v.z, v.w) : empty_key<Key>();
+            }
+        } else {
+            const double2 *v2 = reinterpret_cast<const double2 *>(psi_);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const unsigned long long k0 = b + lane + 32ull * j;
+                double2 v = make_double2(0.0, 0.0);
+                if (k0 < hi) v = v2[k0];
+                k[j] = k0;
+                ok[j] = k0 < hi;
+                p[j] = ok[j] ? key_of(prob_of(v.x, v.y)) : empty_key<Key>();
+            }
         }
-        L.offer(p, k, k < hi);
+        Key mx = p[0];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) mx = mx > p[j] ? mx : p[j];
+        if (!__any_sync(0xffffffffu, mx >= L.wp)) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) L.offer(p[j], k[j], ok[j]);
     }
-    cand_p[warp * 64 + 2 * lane] = L.p0;
-    cand_i[warp * 64 + 2 * lane] = L.i0;
-    cand_p[warp * 64 + 2 * lane + 1] = L.p1;
-    cand_i[warp * 64 + 2 * lane + 1] = L.i1;
+    // merge the block's eight lists in warp 0
+    lp[w][2 * lane] = L.p0; li[w][2 * lane] = L.i0;
+    lp[w][2 * lane + 1] = L.p1; li[w][2 * lane + 1] = L.i1;
+    __syncthreads();
+    if (w == 0) {
+        for (int o = 1; o < 8; ++o)
+            for (int h = 0; h < 2; ++h) {
+                const unsigned long long ci = li[o][32 * h + lane];
+                L.offer(lp[o][32 * h + lane], ci, ci != ~0ull);
+            }
+        // candidates as doubles; empty entries as -1
+        const unsigned long long base = (unsigned long long)blockIdx.x * 64;
+        cand_p[base + 2 * lane] = L.i0 == ~0ull ? -1.0 : value_of(L.p0);
+        cand_i[base + 2 * lane] = L.i0;
+        cand_p[base + 2 * lane + 1] = L.i1 == ~0ull ? -1.0 : value_of(L.p1);
+        cand_i[base + 2 * lane + 1] = L.i1;
+    }
 }
 
-// One warp merges m candidates and writes the best 64, sorted.
-__global__ void topk_pass2(const double *cand_p, const unsigned long long *cand_i,
-                           unsigned long long m, double *out_p, unsigned long long *out_i) {
-    __shared__ double sp[64];
-    __shared__ unsigned long long si[64];
-    const int lane = threadIdx.x & 31;
-    TopList L;
+// Pass 2 (one block of 32 warps): each warp merges a strided share of the m candidates,
+// warp 0 merges the 32 lists and writes the best 64, sorted.
+__global__ void __launch_bounds__(1024) topk_pass2(const double *cand_p, const unsigned long long *cand_i,
+                                                   unsigned long long m, double *out_p,
+                                                   unsigned long long *out_i) {
+    __shared__ unsigned long long sp[32][64];
+    __shared__ unsigned long long si[32][64];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    TopList<unsigned long long> L;
     L.init();
-    for (unsigned long long b = 0; b < m; b += 32) {
+    for (unsigned long long b = (unsigned long long)w * 32; b < m; b += 32ull * 32) {
         const unsigned long long j = b + lane;
         const bool ok = j < m;
-        L.offer(ok ? cand_p[j] : -1.0, ok ? cand_i[j] : ~0ull, ok && cand_p[ok ? j : 0] >= 0.0);
+        const unsigned long long kb = ok ? (unsigned long long)__double_as_longlong(cand_p[j]) : 0ull;
+        const bool real = ok && !(kb >> 63);              // empty entries are -1
+        L.offer(real ? kb : 0ull, real ? cand_i[j] : ~0ull, real);
     }
-    sp[2 * lane] = L.p0; si[2 * lane] = L.i0;
-    sp[2 * lane + 1] = L.p1; si[2 * lane + 1] = L.i1;
+    sp[w][2 * lane] = L.p0; si[w][2 * lane] = L.i0;
+    sp[w][2 * lane + 1] = L.p1; si[w][2 * lane + 1] = L.i1;
+    __syncthreads();
+    if (w != 0) return;
+    for (int o = 1; o < 32; ++o)
+        for (int h = 0; h < 2; ++h) {
+            const unsigned long long ci = si[o][32 * h + lane];
+            L.offer(sp[o][32 * h + lane], ci, ci != ~0ull);
+        }
+    sp[0][2 * lane] = L.p0; si[0][2 * lane] = L.i0;
+    sp[0][2 * lane + 1] = L.p1; si[0][2 * lane + 1] = L.i1;
     __syncwarp();
     if (lane == 0) {
+        unsigned long long *qp = sp[0];
+        unsigned long long *qi = si[0];
         for (int a = 1; a < 64; ++a) {          // insertion sort, best first
-            const double p = sp[a];
-            const unsigned long long ix = si[a];
+            const unsigned long long p = qp[a];
+            const unsigned long long ix = qi[a];
             int b = a - 1;
-            while (b >= 0 && better(p, ix, sp[b], si[b])) {
-                sp[b + 1] = sp[b]; si[b + 1] = si[b];
+            while (b >= 0 && better(p, ix, qp[b], qi[b])) {
+                qp[b + 1] = qp[b]; qi[b + 1] = qi[b];
                 --b;
             }
-            sp[b + 1] = p; si[b + 1] = ix;
+            qp[b + 1] = p; qi[b + 1] = ix;
         }
-        for (int a = 0; a < 64; ++a) { out_p[a] = sp[a]; out_i[a] = si[a]; }
+        for (int a = 0; a < 64; ++a) {
+            out_p[a] = qi[a] == ~0ull ? -1.0 : value_of(qp[a]);
+            out_i[a] = qi[a];
+        }
     }
 }
 
@@ -361,9 +499,21 @@ sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const
                 a.hb = 63 - __builtin_clzll(a.x);
                 a.npairs = 1ull << (s->n - 1);
             }
-            if (s->dtype == SV_C64)
-                svk::expect_kernel<float><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, s->buf, partial);
-            else
+            if (s->dtype == SV_C64) {
+                const float2 *v = reinterpret_cast<const float2 *>(s->buf);
+                const bool pr = a.x != 0;
+                switch (a.nterms) {
+                    case 1: pr ? svk::expect_c64<1, true><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial)
+                               : svk::expect_c64<1, false><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial); break;
+                    case 2: pr ? svk::expect_c64<2, true><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial)
+                               : svk::expect_c64<2, false><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial); break;
+                    case 3: pr ? svk::expect_c64<3, true><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial)
+                               : svk::expect_c64<3, false><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial); break;
+                    case 4: pr ? svk::expect_c64<4, true><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial)
+                               : svk::expect_c64<4, false><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, v, partial); break;
+                    default: svk::expect_kernel<float><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, s->buf, partial);
+                }
+            } else
                 svk::expect_kernel<double><<<nb, svk::RED_THREADS, 0, s->stream>>>(a, s->buf, partial);
             SV_CUDA(cudaGetLastError());
             svk::sum_partials<<<1, svk::RED_THREADS, 0, s->stream>>>(partial, nb, results + nres);
@@ -384,10 +534,10 @@ sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const
 sv_status enqueue_topk(sv_state *s, double *host_p, unsigned long long *host_i) {
     const unsigned long long N = 1ull << s->n;
     const int threads = 256, warps_per_block = threads / 32;
-    int blocks = std::min(s->num_sms * 2, TOPK_MAX_WARPS / warps_per_block);
+    int blocks = std::min(s->num_sms * 4, TOPK_MAX_WARPS / warps_per_block);
     unsigned long long nwarps = (unsigned long long)blocks * warps_per_block;
     unsigned long long chunk = (N + nwarps - 1) / nwarps;
-    chunk = (chunk + 31) / 32 * 32;
+    chunk = (chunk + 255) / 256 * 256;
     double *cp = reinterpret_cast<double *>(s->ws + WS_TOPK);
     unsigned long long *ci = reinterpret_cast<unsigned long long *>(s->ws + WS_TOPK) + TOPK_MAX_WARPS * 64;
     double *op = reinterpret_cast<double *>(s->ws + WS_TOPK + WS_TOPK_BYTES);
@@ -397,7 +547,7 @@ sv_status enqueue_topk(sv_state *s, double *host_p, unsigned long long *host_i) 
     else
         svk::topk_pass1<double><<<blocks, threads, 0, s->stream>>>(s->buf, N, chunk, cp, ci);
     SV_CUDA(cudaGetLastError());
-    svk::topk_pass2<<<1, 32, 0, s->stream>>>(cp, ci, nwarps * 64, op, oi);
+    svk::topk_pass2<<<1, 1024, 0, s->stream>>>(cp, ci, (unsigned long long)blocks * 64, op, oi);
     SV_CUDA(cudaGetLastError());
     SV_CUDA(cudaMemcpyAsync(host_p, op, 64 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     SV_CUDA(cudaMemcpyAsync(host_i, oi, 64 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,

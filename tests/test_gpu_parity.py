@@ -350,3 +350,28 @@ def test_probs_to_host_30q(gpu, dtype):
     del p
     s.free()
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_expectation_term_groups(gpu, dtype):
+    """Groups of 1..5 terms sharing an X-part (the complex64 fast kernels take 1..4 terms
+    per launch, diagonal or not; 5 and more use the general kernel), against the oracle,
+    on a state whose amplitudes span several binades, at sizes with a ragged grid tail."""
+    sv = gpu
+    rng = np.random.default_rng(911 + dtype)
+    for n in (5, 11, 18):
+        psi0 = rand_state(n, rng) * np.exp2(rng.integers(-6, 1, 1 << n))
+        psi0 /= np.linalg.norm(psi0)
+        s = sv.sv_alloc(n, dtype, stream=_torch().cuda.current_stream())
+        psi_in = psi0.astype(np.complex64 if dtype == 0 else np.complex128)
+        sv.sv_set_state(s, psi_in)
+        psi = psi_in.astype(np.complex128)
+        tol = 2e-6 if dtype == 0 else 1e-13
+        for nt in (1, 2, 3, 4, 5, 7):
+            for x in (0, int(rng.integers(1, 1 << n))):
+                zs = [int(v) for v in rng.integers(0, 1 << n, nt)]
+                cs = [float(v) for v in rng.normal(size=nt)]
+                got = sv.sv_expect(s, [x] * nt, zs, cs)
+                want = oracle.expect(psi, [x] * nt, zs, cs)
+                assert abs(got - want) < tol * (1 + sum(abs(c) for c in cs)), (n, nt, x, got, want)
+        s.free()
