@@ -186,7 +186,10 @@ sv_status sv_apply_gate(sv_state *s, const sv_gate *g);
 /* sum_k |alpha_k|^2 accumulated in FP64 (Eq. 1).  Synchronises. */
 sv_status sv_norm(sv_state *s, double *out);
 /* p_k = |alpha_k|^2 for all 2^n outcomes in index order: float (C64) or double (C128).
- * out_on_device: out is device memory (asynchronous) or host memory (synchronises). */
+ * out_on_device: out is device memory (asynchronous) or host memory (synchronises).  Host
+ * memory that is page-locked and mapped for the device (cudaHostAlloc, torch pin_memory)
+ * is written by the kernel directly; other host memory goes through a device temporary of
+ * the same size. */
 sv_status sv_probs(sv_state *s, void *out, int out_on_device);
 /* out = sum_t coef[t] <psi| P_t |psi> for Pauli strings P_t given by xmask[t] (X or Y
  * on those qubits) and zmask[t] (Z or Y): P|k> = i^{|x&z|} (-1)^{|k&z|} |k^x>.

@@ -433,6 +433,16 @@ sv_status sv_probs(sv_state *s, void *out, int out_on_device) {
     clear_error();
     if (!s || !out) return set_error(SV_ERR_ARG, "sv_probs: null argument");
     if (out_on_device) return launch_probs(s, out);
+    // Pinned (page-locked, device-mapped) host memory: the kernel writes it directly over
+    // the CPU-GPU link, with no device temporary and no separate copy.
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr) {
+        const sv_status st = launch_probs(s, pa.devicePointer);
+        if (st != SV_OK) return st;
+        return check_device_error(s);
+    }
+    (void)cudaGetLastError();   // a pageable pointer is not an error
     const size_t bytes = size_t(s->dtype == SV_C64 ? 4 : 8) << s->n;
     void *tmp = nullptr;
     SV_CUDA(cudaMallocAsync(&tmp, bytes, s->stream));

@@ -375,9 +375,10 @@ def sv_norm(s: State) -> float:
 
 
 def sv_probs(s: State, out=None):
-    """Host numpy array (float32 for C64, float64 for C128), or into a CUDA tensor."""
+    """Host numpy array (float32 for C64, float64 for C128), or into a tensor (a CUDA
+    tensor is written asynchronously; a CPU tensor, pinned or not, is host memory)."""
     if out is not None and hasattr(out, "data_ptr"):
-        _check(_lib.sv_probs(s.handle, int(out.data_ptr()), 1))
+        _check(_lib.sv_probs(s.handle, int(out.data_ptr()), 1 if out.is_cuda else 0))
         return out
     n, dt, _ = sv_info(s)
     a = out if out is not None else np.empty(1 << n, dtype=np.float32 if dt == SV_C64 else np.float64)

@@ -375,3 +375,23 @@ def test_expectation_term_groups(gpu, dtype):
                 want = oracle.expect(psi, [x] * nt, zs, cs)
                 assert abs(got - want) < tol * (1 + sum(abs(c) for c in cs)), (n, nt, x, got, want)
         s.free()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_probs_into_pinned_host_memory(gpu, dtype):
+    """Page-locked host output (written by the kernel over the CPU-GPU link) equals the
+    pageable-memory path bit for bit and the oracle's probabilities in the same precision."""
+    sv = gpu
+    torch = _torch()
+    rng = np.random.default_rng(951 + dtype)
+    for n in (9, 22):
+        psi0 = rand_state(n, rng).astype(np.complex64 if dtype == 0 else np.complex128)
+        s = sv.sv_alloc(n, dtype, stream=torch.cuda.current_stream())
+        sv.sv_set_state(s, psi0)
+        pageable = sv.sv_probs(s)
+        pinned = torch.empty(1 << n, dtype=torch.float32 if dtype == 0 else torch.float64).pin_memory()
+        pinned.fill_(-1.0)
+        sv.sv_probs(s, pinned.numpy())
+        assert np.array_equal(pinned.numpy(), pageable)
+        assert np.array_equal(pageable, oracle.probs_in_precision(psi0))
+        s.free()
