@@ -59,21 +59,26 @@
 
 namespace svk {
 
-template <int K>
+// SUB: MMA subtiles (128 groups each) per TMA stage.  SUB = 2 doubles the contiguous
+// segments of launches whose targets are all high (2 KiB instead of 1 KiB at k = 5), at
+// the price of one more A slice in TMEM (A2 2^-9 replaces the B2 2^-9 copy, to fit two
+// 64 KiB stages in shared memory).
+template <int K, int SUB = 1>
 struct TcShape {
     static constexpr uint32_t D = 1u << K;            // amplitudes per group
     static constexpr uint32_t KD = 2u * D;            // real K = N
-    static constexpr uint32_t ROWS = 128;             // groups per tile (MMA M)
-    static constexpr uint32_t TB = K + 7;             // tile bits
-    static constexpr uint32_t TILE_BYTES = ROWS * D * 8u;
+    static constexpr uint32_t ROWS = 128;             // groups per MMA subtile (MMA M)
+    static constexpr uint32_t TB = K + 7 + (SUB == 2 ? 1u : 0u);   // tile bits
+    static constexpr uint32_t TILE_BYTES = SUB * ROWS * D * 8u;
     static constexpr uint32_t B_BYTES = KD * KD * 2u;     // one FP16 slice of B
-    static constexpr uint32_t NB = 4;                     // B1, B2, B3 * 2^-9, B2 * 2^-9
+    static constexpr uint32_t NB = SUB == 2 ? 3u : 4u;    // B1, B2, B3 2^-9 [, B2 2^-9]
     static constexpr uint32_t SBO = (KD / 8u) * 128u;     // 8-row group stride of B
-    static constexpr uint32_t NS = K == 5 ? 3u : 8u;      // raw stages
-    static constexpr uint32_t NOUT = 2u;                  // output staging tiles
+    static constexpr uint32_t NS = SUB == 2 ? 2u : (K == 5 ? 3u : 8u);   // raw stages
+    static constexpr uint32_t NOUT = SUB == 2 ? 1u : 2u;  // output staging tiles
     static constexpr uint32_t ACC = 2u * KD;              // TMEM columns of one D set (D0, D12)
     static constexpr uint32_t A_COLS = KD / 2u;           // TMEM columns of one A slice
-    static constexpr uint32_t A_SET = 3u * A_COLS;        // one A buffer (three slices)
+    static constexpr uint32_t NA = SUB == 2 ? 4u : 3u;    // A1, A2, A3 2^-9 [, A2 2^-9]
+    static constexpr uint32_t A_SET = NA * A_COLS;        // one A buffer
     static constexpr uint32_t A_COL0 = 2u * ACC;          // first column of the A buffers
     static constexpr uint32_t TMEM_COLS = K == 5 ? 512u : 256u;
     static_assert(A_COL0 + 2u * A_SET <= TMEM_COLS, "TMEM layout");
@@ -125,6 +130,12 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     return *reinterpret_cast<const uint32_t *>(&h);
 }
 
+// An FP16 pair times 2^-9 (exact for the integer slices: at most 9 bits, no underflow).
+__device__ __forceinline__ uint32_t half2_times_2m9(uint32_t w) {
+    const __half2 h = __hmul2(*reinterpret_cast<const __half2 *>(&w), __float2half2_rn(1.f / 512.f));
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 // Three 9-bit integer slices of a scaled amplitude (|x scale| < 256): FP16 pairs
 // (re, im) of a1, a2 and a3 2^-9, all exact.
 __device__ __forceinline__ void slice3(float2 v, float scale, uint32_t &w1, uint32_t &w2, uint32_t &w3) {
@@ -140,9 +151,11 @@ __device__ __forceinline__ void slice3(float2 v, float scale, uint32_t &w1, uint
 
 // XP: the launch has targets among tile bits 0..3 and takes members in the lane's XOR
 // order; otherwise every lane takes them in member order (no permutation code at all).
-template <int K, bool XP>
+// The pipelines count tiles (j: raw stage, output staging) and MMA subtiles (js = j SUB +
+// sub: A and D buffers, row scales).
+template <int K, bool XP, int SUB>
 __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
-    using S = TcShape<K>;
+    using S = TcShape<K, SUB>;
     constexpr uint32_t KD = S::KD, NS = S::NS, NOUT = S::NOUT, HALF = S::HALF;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
@@ -187,7 +200,8 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         *reinterpret_cast<__half *>(sB + 1 * S::B_BYTES + off) = __int2half_rn(a.b[1][e]);
         // exact: integers below 2^9 times 2^-9
         *reinterpret_cast<__half *>(sB + 2 * S::B_BYTES + off) = __float2half_rn(a.b[2][e] * (1.f / 512.f));
-        *reinterpret_cast<__half *>(sB + 3 * S::B_BYTES + off) = __float2half_rn(a.b[1][e] * (1.f / 512.f));
+        if constexpr (SUB == 1)
+            *reinterpret_cast<__half *>(sB + 3 * S::B_BYTES + off) = __float2half_rn(a.b[1][e] * (1.f / 512.f));
     }
     fence_proxy_async_smem();
     tc_fence_before();
@@ -241,18 +255,20 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(S::ROWS, KD);
             const uint32_t B0 = smem_u32(sB);
-            uint32_t j = 0;
-            for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
-                const uint32_t b = j & 1u, u = j >> 1;
+            const unsigned long long nsub = a.ntiles > first
+                                                ? ((a.ntiles - first + step - 1) / step) * SUB : 0;
+            for (unsigned long long js = 0; js < nsub; ++js) {
+                const uint32_t b = (uint32_t)js & 1u, u = (uint32_t)(js >> 1);
                 if (!mbar_wait_or_abort(smem_u32(&a_full[b]), u & 1u, abort)) break;
                 if (!mbar_wait_or_abort(smem_u32(&d_empty[b]), (u & 1u) ^ 1u, abort)) break;
                 tc_fence_after();
                 const uint32_t A0 = tmem + S::A_COL0 + b * S::A_SET;
                 const uint32_t dset = tmem + b * S::ACC;
                 // (accumulator, A slice, B slice): D0 = A1 B1; D12 = A1 B2 + A2 B1 +
-                // A1 (B3 2^-9) + A2 (B2 2^-9) + (A3 2^-9) B1   [B slices: B1, B2, B3s, B2s]
-                const uint32_t prod[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0},
-                                             {1, 0, 2}, {1, 1, 3}, {1, 2, 0}};
+                // A1 (B3 2^-9) + A2 (B2 2^-9) + (A3 2^-9) B1   [A slices: A1, A2, A3s, A2s;
+                // B slices: B1, B2, B3s, B2s]; with SUB = 2, A2s B2 stands for A2 B2s
+                const uint32_t prod[6][3] = {{0, 0, 0}, {1, 0, 1}, {1, 1, 0}, {1, 0, 2},
+                                             {1, SUB == 2 ? 3u : 1u, SUB == 2 ? 1u : 3u}, {1, 2, 0}};
 #pragma unroll
                 for (int p = 0; p < 6; ++p) {
                     const uint32_t Aa = A0 + prod[p][1] * S::A_COLS;
@@ -270,66 +286,79 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         }
     } else if (warp < S::W_PROD) {
         // ------------------------------------------------------------ transform
-        // Two warps per TMEM lane quadrant: warp w takes rows 32 (w & 3) .. + 31 and group
-        // members HALF (w >> 2) .. + HALF - 1.
+        // Two warps per TMEM lane quadrant: warp w takes rows 32 (w & 3) .. + 31 of each MMA
+        // subtile and group members HALF (w >> 2) .. + HALF - 1.
         const uint32_t row = (warp & 3u) * 32u + lane;
         const uint32_t part = warp >> 2;
-        const uint32_t gbase = group_base(row);
+        uint32_t gb[SUB];
+#pragma unroll
+        for (uint32_t sub = 0; sub < SUB; ++sub) gb[sub] = group_base(sub * S::ROWS + row);
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         uint32_t cx = 0;
 #pragma unroll
         for (int q = 0; q < K; ++q)
             if ((xl >> q) & 1u) cx |= tbit[q];
         uint32_t j = 0;
-        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+        bool stop = false;
+        for (unsigned long long t = first; t < a.ntiles && !stop; t += step, ++j) {
             const uint32_t s = j % NS;
-            bool ok = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
+            const bool okf = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
             const float2 *rs = reinterpret_cast<const float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
-            // this half of the row (members in the lane's order c ^ x) and its largest component
-            float2 v[HALF];
-            float m = 0.f;
 #pragma unroll
-            for (uint32_t c = 0; c < HALF; ++c) {
-                const uint32_t mo = member_off(part * HALF + c);
-                v[c] = rs[gbase | (XP ? (mo ^ cx) : mo)];
-                m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
-            }
-            max_part[part][row] = m;
-            fence_proxy_async_smem();             // reads of the raw stage before its refill
-            if (!named_bar_and(1, 256, ok)) break;
-            if (tid == 0) mbar_arrive(smem_u32(&empty[s]));
-            m = fmaxf(max_part[0][row], max_part[1][row]);
-            int ex = 0;
-            frexpf(m, &ex);                       // m < 2^ex (m = 0: ex = 0)
-            ex = max(ex, -100);                   // keep 2^(8-ex) finite
-            const float scale = ldexpf(1.f, 8 - ex);   // |x * scale| < 256
-            const uint32_t ab = j & 1u;
-            ok = mbar_wait_or_abort(smem_u32(&a_empty[ab]), ((j >> 1) & 1u) ^ 1u, abort);
-            if (!named_bar_and(1, 256, ok)) break;
-            tc_fence_after();
-            // slot j & 3 was last read by the epilogue of tile j - 4, which finished before
-            // the MMAs of tile j - 2 were issued, whose completion released a_empty[ab]
-            if (part == 0) row_scale[j & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
-            if constexpr (XP) xor_unpermute(v, xl, a.xt);   // back in member order (x < HALF)
-            // three 9-bit integer slices, one FP16 pair (re, im) per 32-bit TMEM column,
-            // stored eight members at a time
-            const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + (((warp & 3u) * 32u) << 16) +
-                                  part * HALF;
+            for (uint32_t sub = 0; sub < SUB; ++sub) {
+                const uint32_t js = j * SUB + sub;
+                const uint32_t gbase = gb[sub];
+                // this half of the row (members in the lane's order c ^ x), its largest component
+                float2 v[HALF];
+                float m = 0.f;
 #pragma unroll
-            for (uint32_t c0 = 0; c0 < HALF; c0 += 8) {
-                uint32_t w1[8], w2[8], w3[8];
+                for (uint32_t c = 0; c < HALF; ++c) {
+                    const uint32_t mo = member_off(part * HALF + c);
+                    v[c] = rs[gbase | (XP ? (mo ^ cx) : mo)];
+                    m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
+                }
+                max_part[part][row] = m;
+                fence_proxy_async_smem();         // reads of the raw stage before its refill
+                if (!named_bar_and(1, 256, okf)) { stop = true; break; }
+                if (sub == SUB - 1 && tid == 0) mbar_arrive(smem_u32(&empty[s]));
+                m = fmaxf(max_part[0][row], max_part[1][row]);
+                int ex = 0;
+                frexpf(m, &ex);                   // m < 2^ex (m = 0: ex = 0)
+                ex = max(ex, -100);               // keep 2^(8-ex) finite
+                const float scale = ldexpf(1.f, 8 - ex);   // |x * scale| < 256
+                const uint32_t ab = js & 1u;
+                const bool oka = mbar_wait_or_abort(smem_u32(&a_empty[ab]), ((js >> 1) & 1u) ^ 1u, abort);
+                if (!named_bar_and(1, 256, oka)) { stop = true; break; }
+                tc_fence_after();
+                // slot js & 3 was last read by the epilogue of subtile js - 4, which finished
+                // before the MMAs of subtile js - 2 were issued, whose completion released
+                // a_empty[ab]
+                if (part == 0) row_scale[js & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
+                if constexpr (XP) xor_unpermute(v, xl, a.xt);   // back in member order (x < HALF)
+                // three 9-bit integer slices (and A2 2^-9 when SUB = 2), one FP16 pair
+                // (re, im) per 32-bit TMEM column, stored eight members at a time
+                const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + (((warp & 3u) * 32u) << 16) +
+                                      part * HALF;
 #pragma unroll
-                for (uint32_t c = 0; c < 8; ++c) slice3(v[c0 + c], scale, w1[c], w2[c], w3[c]);
-                tmem_st8_async(arow + c0, w1);
-                tmem_st8_async(arow + S::A_COLS + c0, w2);
-                tmem_st8_async(arow + 2 * S::A_COLS + c0, w3);
-            }
-            tmem_wait_st();
-            tc_fence_before();
-            named_bar(1, 256);                    // also: max_part is free for the next tile
-            if (tid == 0) {
-                mbar_arrive(smem_u32(&a_full[ab]));
-                mbar_arrive(smem_u32(&scale_full[j & 3u]));
+                for (uint32_t c0 = 0; c0 < HALF; c0 += 8) {
+                    uint32_t w1[8], w2[8], w3[8], w2s[8];
+#pragma unroll
+                    for (uint32_t c = 0; c < 8; ++c) {
+                        slice3(v[c0 + c], scale, w1[c], w2[c], w3[c]);
+                        if constexpr (SUB == 2) w2s[c] = half2_times_2m9(w2[c]);
+                    }
+                    tmem_st8_async(arow + c0, w1);
+                    tmem_st8_async(arow + S::A_COLS + c0, w2);
+                    tmem_st8_async(arow + 2 * S::A_COLS + c0, w3);
+                    if constexpr (SUB == 2) tmem_st8_async(arow + 3 * S::A_COLS + c0, w2s);
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                named_bar(1, 256);                // also: max_part is free for the next subtile
+                if (tid == 0) {
+                    mbar_arrive(smem_u32(&a_full[ab]));
+                    mbar_arrive(smem_u32(&scale_full[js & 3u]));
+                }
             }
         }
     } else if (warp >= S::W_EPI) {
@@ -339,7 +368,9 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         const uint32_t row = quad * 32u + lane;
         const uint32_t et = tid - S::W_EPI * 32u; // 0..255 within the epilogue warps
         const uint32_t part = et >> 7;
-        const uint32_t gbase = group_base(row);
+        uint32_t gb[SUB];
+#pragma unroll
+        for (uint32_t sub = 0; sub < SUB; ++sub) gb[sub] = group_base(sub * S::ROWS + row);
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         uint32_t cx = 0;
 #pragma unroll
@@ -348,40 +379,49 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         SegLanes sl;                              // the first epilogue warp stores segments
         sl.init(a.L, a.h, a.hi, lane);
         uint32_t j = 0;
-        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
-            const uint32_t b = j & 1u, ob = j % NOUT;
-            bool ok = mbar_wait_or_abort(smem_u32(&d_full[b]), (j >> 1) & 1u, abort);
-            ok = ok && mbar_wait_or_abort(smem_u32(&scale_full[j & 3u]), (j >> 2) & 1u, abort);
-            if (!named_bar_and(2, 256, ok)) break;
-            tc_fence_after();
-            if (et < 32) bulk_wait_read<(int)NOUT - 1>();   // this staging tile is free
-            named_bar(2, 256);
-            const float osc = row_scale[j & 3u][row];
+        bool stop = false;
+        for (unsigned long long t = first; t < a.ntiles && !stop; t += step, ++j) {
+            const uint32_t ob = j % NOUT;
             float2 *out = reinterpret_cast<float2 *>(smem + S::OFF_OUT + ob * S::TILE_BYTES);
-            const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16) + part * HALF * 2u;
-            float2 o[HALF];
 #pragma unroll
-            for (uint32_t c0 = 0; c0 < 2u * HALF; c0 += 16) {
-                float d0[16], d12[16];
-                tmem_ld16(lane_addr + c0, d0);
-                tmem_ld16(lane_addr + KD + c0, d12);
-#pragma unroll
-                for (uint32_t i = 0; i < 16; i += 2) {
-                    const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
-                    const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
-                    o[(c0 + i) / 2] = make_float2(re, im);
+            for (uint32_t sub = 0; sub < SUB; ++sub) {
+                const uint32_t js = j * SUB + sub, b = js & 1u;
+                bool ok = mbar_wait_or_abort(smem_u32(&d_full[b]), (js >> 1) & 1u, abort);
+                ok = ok && mbar_wait_or_abort(smem_u32(&scale_full[js & 3u]), (js >> 2) & 1u, abort);
+                if (!named_bar_and(2, 256, ok)) { stop = true; break; }
+                tc_fence_after();
+                if (sub == 0) {
+                    if (et < 32) bulk_wait_read<(int)NOUT - 1>();   // this staging tile is free
+                    named_bar(2, 256);
                 }
-            }
-            if constexpr (XP) xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < HALF)
+                const uint32_t gbase = gb[sub];
+                const float osc = row_scale[js & 3u][row];
+                const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16) + part * HALF * 2u;
+                float2 o[HALF];
 #pragma unroll
-            for (uint32_t c = 0; c < HALF; ++c) {
-                const uint32_t mo = member_off(part * HALF + c);
-                out[gbase | (XP ? (mo ^ cx) : mo)] = o[c];
+                for (uint32_t c0 = 0; c0 < 2u * HALF; c0 += 16) {
+                    float d0[16], d12[16];
+                    tmem_ld16(lane_addr + c0, d0);
+                    tmem_ld16(lane_addr + KD + c0, d12);
+#pragma unroll
+                    for (uint32_t i = 0; i < 16; i += 2) {
+                        const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
+                        const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
+                        o[(c0 + i) / 2] = make_float2(re, im);
+                    }
+                }
+                if constexpr (XP) xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < HALF)
+#pragma unroll
+                for (uint32_t c = 0; c < HALF; ++c) {
+                    const uint32_t mo = member_off(part * HALF + c);
+                    out[gbase | (XP ? (mo ^ cx) : mo)] = o[c];
+                }
+                tc_fence_before();
+                fence_proxy_async_smem();
+                named_bar(2, 256);
+                if (et == 0) mbar_arrive(smem_u32(&d_empty[b]));
             }
-            tc_fence_before();
-            fence_proxy_async_smem();
-            named_bar(2, 256);
-            if (et == 0) mbar_arrive(smem_u32(&d_empty[b]));
+            if (stop) break;
             if (et < 32) {
                 if (lane < nseg)
                     bulk_s2g(psi + sl.base(t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
@@ -400,21 +440,35 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
 
 template <int K>
 sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
-    using S = TcShape<K>;
+    using S = TcShape<K, 1>;
+    using S2 = TcShape<K, 2>;
     constexpr uint32_t D = S::D, KD = S::KD;
     static std::once_flag once;
     static cudaError_t init_err = cudaSuccess;
     std::call_once(once, [] {
-        init_err = cudaFuncSetAttribute(apply_tc<K, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        init_err = cudaFuncSetAttribute(apply_tc<K, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)S::SMEM);
         if (init_err == cudaSuccess)
-            init_err = cudaFuncSetAttribute(apply_tc<K, true>,
+            init_err = cudaFuncSetAttribute(apply_tc<K, true, 1>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if constexpr (K == 5) {
+            if (init_err == cudaSuccess)
+                init_err = cudaFuncSetAttribute(apply_tc<K, false, 2>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S2::SMEM);
+        }
     });
     if (init_err != cudaSuccess)
         return svi::set_error(SV_ERR_CUDA, std::string("tensor-core kernel setup: ") +
                                                cudaGetErrorString(init_err));
-    const Plan p = make_plan(s->n, K, g.t, S::TB);
+    Plan p = make_plan(s->n, K, g.t, S::TB);
+    // 8-byte accesses: bank pair = tile bits 0..3; targets there get lane-dependent order
+    uint32_t tl = 0;
+    while (tl < (uint32_t)K && p.lp[tl] < 4u) ++tl;
+    // width 5 without targets in the bank bits: two subtiles per stage (segments twice as
+    // long, half the per-stage work): all targets high 0.82 -> 0.68 ms at 28 qubits,
+    // contiguous 0.70 -> 0.68; the XOR-order variant is slower that way (0.76 -> 0.83)
+    const bool wide = K == 5 && tl == 0 && s->n >= S2::TB;
+    if (wide) p = make_plan(s->n, K, g.t, S2::TB);
     TcArgs<K> a;
     // R (real embedding of U) and its fixed-point slices, in FP64 on the host
     double rmax = 0.0;
@@ -445,15 +499,17 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     a.h = p.h;
     for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
     for (int j = 0; j < K; ++j) a.lp[j] = p.lp[j];
-    // 8-byte accesses: bank pair = tile bits 0..3; targets there get lane-dependent order
-    uint32_t tl = 0;
-    while (tl < (uint32_t)K && p.lp[tl] < 4u) ++tl;
     a.xs = 4u - tl;
     a.xt = std::min(tl, (uint32_t)K - 1u);   // permute within a worker's half of the members
     const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
     // with eight worker warps per role the permutation costs less than even 2-way conflicts
-    if (a.xt >= 1) apply_tc<K, true><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
-    else apply_tc<K, false><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    if (wide) {
+        if constexpr (K == 5) apply_tc<K, false, 2><<<grid, S2::THREADS, S2::SMEM, s->stream>>>(a);
+    } else if (a.xt >= 1) {
+        apply_tc<K, true, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    } else {
+        apply_tc<K, false, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    }
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }
@@ -471,7 +527,7 @@ bool tc_eligible(const sv_state *s, const Gate &g) {
 // moves a tile with half the per-tile overhead of the k = 4 one for the same bytes.
 sv_status launch_apply_tc(sv_state *s, const Gate &g) {
     if (g.k == 5) return svk::launch_tc_t<5>(s, g);
-    if (s->n >= svk::TcShape<5>::TB) return svk::launch_tc_t<5>(s, widen_gate(g, s->n, 5));
+    if (s->n >= svk::TcShape<5, 1>::TB) return svk::launch_tc_t<5>(s, widen_gate(g, s->n, 5));
     return svk::launch_tc_t<4>(s, g);
 }
 
