@@ -42,11 +42,11 @@ FALLBACK_HBM_GBS = 6800.0
 # as null once those sources hash differently).
 KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
-            "sha256_prefix": "37cb841824dd087f", "n": 30,
-            "bytes_per_launch": (1.073818e9 + 1.011945e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,*> 74.8% of GPU time, all apply kernels "
-                      "97.5% (profiles/fused_pass_grid30q_k5_launches.md)",
-            "traffic_source": "apply_tc<5,0> ncu capture at 27q scaled to 30q "
+            "sha256_prefix": "3cf35838b811e8b1", "n": 30,
+            "bytes_per_launch": (1.073832e9 + 1.013200e9) * 8,
+            "kernel": "fused-gate passes: apply_tc<5,*,*> 72.7% of GPU time, all apply kernels "
+                      "97.2% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "traffic_source": "apply_tc<5,0,2> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
              "sha256_prefix": "3b3b6ab080f4a077", "n": 30,
