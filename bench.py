@@ -91,6 +91,21 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(ms, world, device):
+    """The job's time is its slowest rank's: all-reduce MAX of the per-rank milliseconds."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, ms):
+    """Whole-job units per second: every rank ran `steps` units in at most `ms`."""
+    return world * steps / (ms / 1000.0)
+
+
 def kernel_sha(files):
     h = hashlib.sha256()
     for f in files:
@@ -439,11 +454,7 @@ def main():
             torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         clocks = clk.summary()
 
         # dominant kernel: the apply passes, timed with CUDA events on the state's stream
@@ -508,7 +519,7 @@ def main():
     state.free()
     if rank != 0:
         return
-    value = world * args.steps / (ms / 1000.0)
+    value = job_throughput(world, args.steps, ms)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_baseline(specs, args.n, args.cpu_sample_s, len(specs))
