@@ -13,6 +13,8 @@ Contents (each function cites the passage it follows):
 * fusion.py    -- DAG construction and Algorithm 2 (Section 5.1-5.2, Eqs. 8-9).
 * precision.py -- the a-priori precision rule (Eqs. 11-12).
 * brute.py     -- Kronecker forms used to pin the loops at n <= 10 (Eq. 3).
+* sampling.py  -- measurement sampling (the backend's third operation, Section 4.1): block
+  prefix sums in a fixed order and SplitMix64 counters.
 
 Parity status: apply, norm, probabilities, Pauli expectation, top-k, fusion and the
 precision rule are all pinned by tests under tests/test_oracle_*.py (closed forms,
@@ -29,7 +31,7 @@ from typing import Iterable, List, Sequence, Tuple
 
 import numpy as np
 
-from . import brute, fusion, gates, precision  # noqa: F401
+from . import brute, fusion, gates, precision, sampling  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sv_oracle.c")
