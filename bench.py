@@ -74,9 +74,11 @@ def parse():
     ap.add_argument("--compare-unfused", action="store_true",
                     help="also time the unfused complex128 per-gate form once")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
-    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve"],
+    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve", "sample"],
                     help="single: the 30-qubit hot path (default line); batched: 512 HEA "
-                         "circuits of 16-22 qubits; serve: Poisson request stream")
+                         "circuits of 16-22 qubits; serve: Poisson request stream; sample: "
+                         "measurement shots from the 30-qubit circuit's output state")
+    ap.add_argument("--shots", type=int, default=1 << 20, help="sample: shots per step")
     ap.add_argument("--count", type=int, default=512, help="batched: number of circuits")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serve: req/s list")
     ap.add_argument("--duration", type=float, default=4.0, help="serve: seconds per rate")
@@ -241,6 +243,52 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sample(args):
+    """Measurement sampling (sv_sample) from the output state of the 30-qubit grid circuit:
+    one step = one sv_sample call of --shots shots to host memory (block sums over the
+    whole state, prefix sums, the shots)."""
+    import torch
+    from paper_2604_03816_gb300 import sv
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    dt = sv.SV_C64 if args.dtype == "c64" else sv.SV_C128
+    specs = W.grid_random(args.n, args.cycles)
+    state = sv.sv_alloc(args.n, dt, stream=stream)
+    with torch.cuda.stream(stream):
+        sv.sv_apply_circuit(state, sv.sv_fuse(sv.gates_from_specs(specs), args.n, args.k))
+        for w in range(args.warmup):
+            sv.sv_sample(state, w, args.shots)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(None) as clk:
+            e0.record(stream)
+            for i in range(args.steps):
+                shots = sv.sv_sample(state, 1000 + i, args.shots)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+    state.free()
+    sbytes = (8 if dt == sv.SV_C64 else 16) << args.n
+    peak, peak_kind = hbm_peak()
+    out = {"metric": "measurement shots/s (sv_sample, 30q grid circuit output state)",
+           "value": args.shots / (ms / 1000.0), "unit": "shots/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64 sums", "data": "synthetic",
+           "config": {"workload": f"grid_random {args.n}q depth {args.cycles}, {args.dtype}, "
+                                  f"{args.shots} shots per call to host memory",
+                      "state_bytes": sbytes, "seed": W.seed_for(3, args.n),
+                      "l2": "state larger than L2 (inputs > 129 MB), no flush needed"},
+           "roofline": {"bound": "hbm", "achieved": sbytes / (ms / 1000.0) / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": sbytes / (ms / 1000.0) / 1e9 / peak,
+                        "traffic": None, "peak_kind": peak_kind,
+                        "kernel": "whole call (one read of the state for the FP64 block "
+                                  "sums, then prefix and shots)"},
+           "cpu_baseline": None, "e2e": None, "gpu_launches": 4 * args.steps,
+           "clocks": clk.summary(), "last_shots_head": [int(v) for v in shots[:4]]}
+    print(json.dumps(out), flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals (each rate in --rates) of seeded brickwork circuits, width
     U{10..30}, depth U{10..60}, 70% complex64 / 30% complex128, top-64 outcomes, under a
@@ -398,6 +446,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "sample":
+        run_sample(args)
         return
     rank, world, local = dist_info()
     import torch

@@ -196,6 +196,18 @@ sv_status sv_probs(sv_state *s, void *out, int out_on_device);
  * Accumulated in FP64.  Synchronises. */
 sv_status sv_expect(sv_state *s, const uint64_t *xmask, const uint64_t *zmask,
                     const double *coef, size_t nterms, double *out);
+/* Measurement sampling, the backend's third operation (Section 4.1; the paper prints no
+ * procedure): nshots outcome indices drawn from p_k = |alpha_k|^2 / sum_j |alpha_j|^2.
+ * Fixed procedure, reproducible bit for bit: p_k in the state's precision widened to
+ * FP64; FP64 block sums over 64 outcomes in index order; chunk-local exclusive prefixes
+ * of 4096 blocks plus the exclusive prefix of the chunk totals (index order), T = total;
+ * shot i: u = (SplitMix64(seed + (i+1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53, target =
+ * u * T; the largest block whose prefix is <= target and whose sum is > 0, then the first
+ * outcome of the block whose running sum exceeds target - prefix (else its last outcome
+ * with p > 0).  Outcomes with p = 0 are never drawn.
+ * out: nshots uint64 (host or device memory per out_on_device).  Temporary device memory:
+ * 2^n / 4 bytes.  SV_ERR_STATE if the state has zero norm.  Synchronises for host output. */
+sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64_t *out, int out_on_device);
 /* The min(k, 2^n) most probable outcomes (1 <= k <= 64), sorted by probability
  * descending, ties to the lower index.  idx/p are host arrays of k entries.  Synchronises. */
 sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);

@@ -35,7 +35,7 @@ EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
            "sv_expect_noalloc"]
-EXPORTS += ["sv_fuse_like"]
+EXPORTS += ["sv_fuse_like", "sv_sample"]
 EXPORTS += ["sv_server_create", "sv_server_submit", "sv_server_poll", "sv_server_get_stats",
             "sv_server_destroy"]
 EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_get_state",
@@ -128,6 +128,7 @@ _sig = {
     "sv_probs": [_vp, _vp, _i32],
     "sv_expect": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp, ctypes.c_size_t, _dp],
     "sv_topk": [_vp, _u32, ctypes.POINTER(_u64), _dp],
+    "sv_sample": [_vp, _u64, ctypes.c_size_t, ctypes.POINTER(_u64), ctypes.c_int],
     "sv_sync": [_vp],
     "sv_set_policy": [_vp, _u32],
     "sv_server_create": [ctypes.POINTER(sv_server_config), ctypes.POINTER(_vp)],
@@ -420,6 +421,18 @@ def sv_topk(s: State, k: int = 64) -> Tuple[np.ndarray, np.ndarray]:
     p = np.zeros(k, dtype=np.float64)
     _check(_lib.sv_topk(s.handle, k, idx.ctypes.data_as(ctypes.POINTER(_u64)), _ptr(p)))
     return idx[:m], p[:m]
+
+
+def sv_sample(s: State, seed: int, nshots: int, out=None) -> np.ndarray:
+    """nshots sampled outcome indices (uint64); into a CUDA tensor if given one."""
+    if out is not None and hasattr(out, "data_ptr") and out.is_cuda:
+        _check(_lib.sv_sample(s.handle, seed & ((1 << 64) - 1), nshots,
+                              ctypes.cast(int(out.data_ptr()), ctypes.POINTER(_u64)), 1))
+        return out
+    a = np.empty(nshots, dtype=np.uint64)
+    _check(_lib.sv_sample(s.handle, seed & ((1 << 64) - 1), nshots,
+                          a.ctypes.data_as(ctypes.POINTER(_u64)), 0))
+    return a
 
 
 def sv_set_policy(s: State, flags: int) -> None:
