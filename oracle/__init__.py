@@ -15,6 +15,8 @@ Contents (each function cites the passage it follows):
 * brute.py     -- Kronecker forms used to pin the loops at n <= 10 (Eq. 3).
 * sampling.py  -- measurement sampling (the backend's third operation, Section 4.1): block
   prefix sums in a fixed order and SplitMix64 counters.
+* density.py   -- density matrices with single-qubit depolarizing noise after every gate
+  (Section 9.5, Table 8).
 
 Parity status: apply, norm, probabilities, Pauli expectation, top-k, fusion and the
 precision rule are all pinned by tests under tests/test_oracle_*.py (closed forms,
@@ -31,7 +33,7 @@ from typing import Iterable, List, Sequence, Tuple
 
 import numpy as np
 
-from . import brute, fusion, gates, precision, sampling  # noqa: F401
+from . import brute, density, fusion, gates, precision, sampling  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sv_oracle.c")
