@@ -74,11 +74,14 @@ def parse():
     ap.add_argument("--compare-unfused", action="store_true",
                     help="also time the unfused complex128 per-gate form once")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
-    ap.add_argument("--mode", default="single", choices=["single", "batched", "serve", "sample"],
+    ap.add_argument("--mode", default="single",
+                    choices=["single", "batched", "serve", "sample", "noise"],
                     help="single: the 30-qubit hot path (default line); batched: 512 HEA "
                          "circuits of 16-22 qubits; serve: Poisson request stream; sample: "
                          "measurement shots from the 30-qubit circuit's output state")
     ap.add_argument("--shots", type=int, default=1 << 20, help="sample: shots per step")
+    ap.add_argument("--p-depol", type=float, default=0.01, help="noise: depolarizing p")
+    ap.add_argument("--noise-n", type=int, default=15, help="noise: qubits of the density matrix")
     ap.add_argument("--count", type=int, default=512, help="batched: number of circuits")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serve: req/s list")
     ap.add_argument("--duration", type=float, default=4.0, help="serve: seconds per rate")
@@ -289,6 +292,72 @@ def run_sample(args):
     print(json.dumps(out), flush=True)
 
 
+def run_noise(args):
+    """Noisy simulation (Section 9.5): the grid circuit on --noise-n qubits with single-qubit
+    depolarizing noise after every gate, as a density matrix (a vector of 2 x n qubits).
+    One step = sv_fuse_density + sv_set_basis + sv_apply_circuit + sv_density_probs to
+    host; F_cl and TVD against the noiseless distribution are reported."""
+    import torch
+    from paper_2604_03816_gb300 import sv
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    dt = sv.SV_C64 if args.dtype == "c64" else sv.SV_C128
+    n = args.noise_n
+    specs = W.grid_random(n, args.cycles)
+    gates = sv.gates_from_specs(specs)
+    state = sv.sv_alloc(2 * n, dt, stream=stream)
+    k = min(args.k, 4)
+    with torch.cuda.stream(stream):
+        def step(timing=False):
+            c = sv.sv_fuse_density(gates, n, args.p_depol, k)
+            sv.sv_set_basis(state, 0)
+            rep = sv.sv_apply_circuit(state, c, timing=timing)
+            return rep, sv.sv_density_probs(state), len(c)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = []
+        with ClockSampler(None) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                rep, pr, nfused = step(timing=True)
+                reps.append(rep)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        ideal_state = sv.sv_alloc(n, sv.SV_C128, stream=stream)
+        sv.sv_apply_circuit(ideal_state, sv.sv_fuse(gates, n, 4))
+        ideal = sv.sv_probs(ideal_state).astype(np.float64)
+        ideal_state.free()
+    state.free()
+    apply_ms = sum(r["apply_ms"] for r in reps)
+    abytes = sum(r["bytes"] for r in reps)
+    achieved = abytes / (apply_ms / 1000.0) / 1e9
+    peak, peak_kind = hbm_peak()
+    pr = pr.astype(np.float64)
+    out = {"metric": "noisy circuits/s (density matrix, depolarizing after every gate)",
+           "value": 1000.0 / ms, "unit": "circuits/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if dt == sv.SV_C64 else "f64", "data": "synthetic",
+           "config": {"workload": f"grid_random {n}q depth {args.cycles} with depolarizing "
+                                  f"p={args.p_depol} after every gate, density matrix as a "
+                                  f"{2 * n}-qubit {args.dtype} vector, fused k={k}",
+                      "gates": len(specs), "fused_gates": nfused, "seed": W.seed_for(3, n),
+                      "state_bytes": (8 if dt == sv.SV_C64 else 16) << (2 * n),
+                      "l2": "state larger than L2, no flush needed"},
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                        "kernel": "fused-gate passes on the density vector"},
+           "result": {"trace": float(pr.sum()),
+                      "F_cl_vs_noiseless": float(np.sum(np.sqrt(np.clip(pr, 0, None) * ideal)) ** 2),
+                      "TVD_vs_noiseless": float(0.5 * np.sum(np.abs(pr - ideal)))},
+           "cpu_baseline": None, "e2e": None,
+           "gpu_launches": (reps[-1]["passes"] + 2) * args.steps, "clocks": clk.summary()}
+    print(json.dumps(out), flush=True)
+
+
 def run_serve(args):
     """Poisson arrivals (each rate in --rates) of seeded brickwork circuits, width
     U{10..30}, depth U{10..60}, 70% complex64 / 30% complex128, top-64 outcomes, under a
@@ -449,6 +518,9 @@ def main():
         return
     if args.mode == "sample":
         run_sample(args)
+        return
+    if args.mode == "noise":
+        run_noise(args)
         return
     rank, world, local = dist_info()
     import torch

@@ -196,6 +196,20 @@ sv_status sv_probs(sv_state *s, void *out, int out_on_device);
  * Accumulated in FP64.  Synchronises. */
 sv_status sv_expect(sv_state *s, const uint64_t *xmask, const uint64_t *zmask,
                     const double *coef, size_t nterms, double *out);
+/* Noisy simulation with density matrices (Section 9.5): rho on n <= 17 qubits is the
+ * 2n-qubit vector v[r + 2^n c] = rho[r, c] (row bits low, column bits high), a state of
+ * width 2n made with sv_alloc(2n, ...) and started with sv_set_basis(s, 0) = |0..0><0..0|.
+ * sv_fuse_density builds, for every gate U on T, the pair U on T (rows) and conj(U) on
+ * T + n (columns), then for each target q the single-qubit depolarizing channel
+ * rho -> (1 - p) rho + (p/3)(X rho X + Y rho Y + Z rho Z) as a 4 x 4 matrix on the bits
+ * (q, q + n); and fuses the list on 2n qubits by Algorithm 2 (max_k as in sv_fuse).  The
+ * result is applied with sv_apply_circuit (adaptive precision does not apply: the norm of
+ * v is not conserved).  0 <= p <= 1; n in 1..17. */
+sv_status sv_fuse_density(const sv_gate *gates, size_t ngates, uint32_t n, double p, uint32_t max_k,
+                          sv_circuit **out);
+/* p(x) = Re rho[x, x] for x < 2^(width/2) of a vectorised density matrix (even width):
+ * float (C64) or double (C128); host or device memory as in sv_probs. */
+sv_status sv_density_probs(sv_state *s, void *out, int out_on_device);
 /* Measurement sampling, the backend's third operation (Section 4.1; the paper prints no
  * procedure): nshots outcome indices drawn from p_k = |alpha_k|^2 / sum_j |alpha_j|^2.
  * Fixed procedure, reproducible bit for bit: p_k in the state's precision widened to

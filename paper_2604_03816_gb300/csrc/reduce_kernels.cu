@@ -113,6 +113,16 @@ __global__ void probs_c128(const double2 *__restrict__ v, unsigned long long n, 
         out[i] = prob_of(v[i].x, v[i].y);
 }
 
+// Diagonal of a density matrix held as the 2m-qubit vector v[r + 2^m c] = rho[r, c]:
+// p(x) = Re rho[x, x] = Re v[x (2^m + 1)], in the state's precision.
+template <typename C, typename R>
+__global__ void density_diag(const C *__restrict__ v, uint32_t m, R *__restrict__ out) {
+    const unsigned long long M = 1ull << m;
+    for (unsigned long long x = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; x < M;
+         x += (unsigned long long)gridDim.x * blockDim.x)
+        out[x] = v[x * (M + 1)].x;
+}
+
 // ---------------------------------------------------------------- Pauli expectation
 
 constexpr int EXP_MAX_TERMS = 32;
@@ -461,6 +471,19 @@ sv_status launch_probs(sv_state *s, void *dev_out) {
     else
         svk::probs_c128<<<nb, 256, 0, s->stream>>>(reinterpret_cast<const double2 *>(s->buf), N,
                                                     reinterpret_cast<double *>(dev_out));
+    SV_CUDA(cudaGetLastError());
+    return SV_OK;
+}
+
+sv_status launch_density_probs(sv_state *s, void *dev_out) {
+    const uint32_t m = s->n / 2;
+    const int nb = s->num_sms * 8;
+    if (s->dtype == SV_C64)
+        svk::density_diag<<<nb, 256, 0, s->stream>>>(reinterpret_cast<const float2 *>(s->buf), m,
+                                                     reinterpret_cast<float *>(dev_out));
+    else
+        svk::density_diag<<<nb, 256, 0, s->stream>>>(reinterpret_cast<const double2 *>(s->buf), m,
+                                                     reinterpret_cast<double *>(dev_out));
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }

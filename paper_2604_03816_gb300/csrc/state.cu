@@ -193,6 +193,29 @@ sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device) {
     return SV_OK;
 }
 
+// A circuit object holding Algorithm 2's schedule of `in` and what sv_fuse_like needs.
+static sv_status make_circuit(const std::vector<Gate> &in, uint32_t n, uint32_t max_k, sv_circuit **out,
+                              const char *who) {
+    sv_circuit *c = new (std::nothrow) sv_circuit();
+    if (!c) return set_error(SV_ERR_OOM, std::string(who) + ": host allocation failed");
+    c->n = n;
+    try {
+        c->max_k = max_k;
+        c->in_k.reserve(in.size());
+        c->in_t.reserve(in.size() * SV_MAX_K);
+        for (const Gate &g : in) {
+            c->in_k.push_back(g.k);
+            for (uint32_t j = 0; j < SV_MAX_K; ++j) c->in_t.push_back(j < g.k ? g.t[j] : 0);
+        }
+        c->gates = fuse_gates(in, n, max_k, &c->plan);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return set_error(SV_ERR_OOM, std::string(who) + ": host allocation failed");
+    }
+    *out = c;
+    return SV_OK;
+}
+
 sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k,
                   sv_circuit **out) {
     clear_error();
@@ -208,24 +231,57 @@ sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_
         if (st != SV_OK) return set_error(st, sv_last_error() + (" (gate " + std::to_string(i) + ")"));
         in.push_back(sorted_gate(gates[i].k, gates[i].targets, gates[i].u));
     }
-    sv_circuit *c = new (std::nothrow) sv_circuit();
-    if (!c) return set_error(SV_ERR_OOM, "sv_fuse: host allocation failed");
-    c->n = n;
-    try {
-        c->max_k = max_k;
-        c->in_k.reserve(in.size());
-        c->in_t.reserve(in.size() * SV_MAX_K);
-        for (const Gate &g : in) {
-            c->in_k.push_back(g.k);
-            for (uint32_t j = 0; j < SV_MAX_K; ++j) c->in_t.push_back(j < g.k ? g.t[j] : 0);
+    return make_circuit(in, n, max_k, out, "sv_fuse");
+}
+
+// Density matrices with single-qubit depolarizing noise (Section 9.5): rho on n qubits as
+// the 2n-qubit vector v[r + 2^n c] = rho[r, c].  rho -> U rho U^dagger is U on the row bits
+// T and conj(U) on the column bits T + n; the channel (1 - p) rho + (p/3)(X rho X + Y rho Y
+// + Z rho Z) on qubit q is the 4 x 4 matrix (1 - p) I + (p/3) sum_P conj(P) (x) P on the
+// bits (q, q + n) (local bit 0 = row bit q), applied to each target right after the gate.
+sv_status sv_fuse_density(const sv_gate *gates, size_t ngates, uint32_t n, double p, uint32_t max_k,
+                          sv_circuit **out) {
+    clear_error();
+    if (!out) return set_error(SV_ERR_ARG, "sv_fuse_density: null out");
+    *out = nullptr;
+    if (n < 1 || 2 * n > SV_MAX_QUBITS)
+        return set_error(SV_ERR_ARG, "sv_fuse_density: n must be 1..17 (2n <= 34 vector qubits)");
+    if (max_k > SV_MAX_K) return set_error(SV_ERR_ARG, "sv_fuse_density: max_k must be 0..5");
+    if (!(p >= 0.0 && p <= 1.0)) return set_error(SV_ERR_ARG, "sv_fuse_density: p must be in [0, 1]");
+    if (ngates && !gates) return set_error(SV_ERR_ARG, "sv_fuse_density: null gates");
+    // the channel's superoperator on (row bit, column bit), index l = r + 2 c
+    const cplx I(0.0, 1.0);
+    const cplx P[3][2][2] = {{{0.0, 1.0}, {1.0, 0.0}}, {{0.0, -I}, {I, 0.0}}, {{1.0, 0.0}, {0.0, -1.0}}};
+    std::vector<cplx> chan(16, cplx(0.0, 0.0));
+    for (int l2 = 0; l2 < 4; ++l2)
+        for (int l = 0; l < 4; ++l) {
+            const int r2 = l2 & 1, c2 = l2 >> 1, r = l & 1, c = l >> 1;
+            cplx v = l2 == l ? cplx(1.0 - p, 0.0) : cplx(0.0, 0.0);
+            for (int q = 0; q < 3; ++q) v += (p / 3.0) * P[q][r2][r] * std::conj(P[q][c2][c]);
+            chan[l2 * 4 + l] = v;
         }
-        c->gates = fuse_gates(in, n, max_k, &c->plan);
-    } catch (const std::bad_alloc &) {
-        delete c;
-        return set_error(SV_ERR_OOM, "sv_fuse: host allocation failed");
+    std::vector<Gate> in;
+    in.reserve(ngates * 4);
+    for (size_t i = 0; i < ngates; ++i) {
+        sv_status st = validate_gate(&gates[i], n, "sv_fuse_density");
+        if (st != SV_OK) return set_error(st, sv_last_error() + (" (gate " + std::to_string(i) + ")"));
+        const Gate g = sorted_gate(gates[i].k, gates[i].targets, gates[i].u);
+        Gate gc = g;
+        for (uint32_t j = 0; j < g.k; ++j) gc.t[j] = g.t[j] + n;
+        for (cplx &v : gc.u) v = std::conj(v);
+        in.push_back(g);
+        in.push_back(gc);
+        if (p > 0.0)
+            for (uint32_t j = 0; j < g.k; ++j) {
+                Gate d;
+                d.k = 2;
+                d.t[0] = g.t[j];
+                d.t[1] = g.t[j] + n;
+                d.u = chan;
+                in.push_back(d);
+            }
     }
-    *out = c;
-    return SV_OK;
+    return make_circuit(in, 2 * n, max_k, out, "sv_fuse_density");
 }
 
 sv_status sv_fuse_like(const sv_circuit *pattern, const sv_gate *gates, size_t ngates, sv_circuit **out) {
@@ -447,6 +503,32 @@ sv_status sv_probs(sv_state *s, void *out, int out_on_device) {
     void *tmp = nullptr;
     SV_CUDA(cudaMallocAsync(&tmp, bytes, s->stream));
     sv_status st = launch_probs(s, tmp);
+    if (st == SV_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
+        if (e != cudaSuccess) st = set_error(SV_ERR_CUDA, cudaGetErrorString(e));
+    }
+    cudaFreeAsync(tmp, s->stream);
+    if (st != SV_OK) return st;
+    return check_device_error(s);
+}
+
+sv_status sv_density_probs(sv_state *s, void *out, int out_on_device) {
+    clear_error();
+    if (!s || !out) return set_error(SV_ERR_ARG, "sv_density_probs: null argument");
+    if (s->n % 2) return set_error(SV_ERR_ARG, "sv_density_probs: the state is not a vectorised density matrix (odd width)");
+    if (out_on_device) return launch_density_probs(s, out);
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr) {
+        const sv_status st = launch_density_probs(s, pa.devicePointer);
+        if (st != SV_OK) return st;
+        return check_device_error(s);
+    }
+    (void)cudaGetLastError();
+    const size_t bytes = size_t(s->dtype == SV_C64 ? 4 : 8) << (s->n / 2);
+    void *tmp = nullptr;
+    SV_CUDA(cudaMallocAsync(&tmp, bytes, s->stream));
+    sv_status st = launch_density_probs(s, tmp);
     if (st == SV_OK) {
         cudaError_t e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, s->stream);
         if (e != cudaSuccess) st = set_error(SV_ERR_CUDA, cudaGetErrorString(e));

@@ -108,6 +108,7 @@ bool tc64_eligible(const sv_state *s, const Gate &g);      // apply_tc64.cu
 sv_status launch_apply_tc64(sv_state *s, const Gate &g);
 sv_status launch_norm(sv_state *s, double *dev_out);     // writes one double on device
 sv_status launch_probs(sv_state *s, void *dev_out);
+sv_status launch_density_probs(sv_state *s, void *dev_out);   // Re v[x + 2^(n/2) x]
 sv_status launch_expect(sv_state *s, const uint64_t *x, const uint64_t *z, const double *c,
                         size_t nterms, double *host_out);
 sv_status launch_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);

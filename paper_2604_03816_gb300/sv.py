@@ -35,7 +35,7 @@ EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
            "sv_expect_noalloc"]
-EXPORTS += ["sv_fuse_like", "sv_sample"]
+EXPORTS += ["sv_fuse_like", "sv_sample", "sv_fuse_density", "sv_density_probs"]
 EXPORTS += ["sv_server_create", "sv_server_submit", "sv_server_poll", "sv_server_get_stats",
             "sv_server_destroy"]
 EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_get_state",
@@ -117,6 +117,8 @@ _sig = {
     "sv_set_state": [_vp, _vp, _i32],
     "sv_get_state": [_vp, _vp, _i32],
     "sv_fuse": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32, ctypes.POINTER(_vp)],
+    "sv_fuse_density": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, ctypes.c_double, _u32,
+                        ctypes.POINTER(_vp)],
     "sv_circuit_free": [_vp],
     "sv_fuse_like": [_vp, ctypes.POINTER(sv_gate), ctypes.c_size_t, ctypes.POINTER(_vp)],
     "sv_circuit_size": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_u32)],
@@ -129,6 +131,7 @@ _sig = {
     "sv_expect": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp, ctypes.c_size_t, _dp],
     "sv_topk": [_vp, _u32, ctypes.POINTER(_u64), _dp],
     "sv_sample": [_vp, _u64, ctypes.c_size_t, ctypes.POINTER(_u64), ctypes.c_int],
+    "sv_density_probs": [_vp, _vp, ctypes.c_int],
     "sv_sync": [_vp],
     "sv_set_policy": [_vp, _u32],
     "sv_server_create": [ctypes.POINTER(sv_server_config), ctypes.POINTER(_vp)],
@@ -231,6 +234,25 @@ def sv_fuse(gates, n: int, max_k: int) -> Circuit:
     h = _vp()
     _check(_lib.sv_fuse(ga.arr, ga.n, n, max_k, ctypes.byref(h)))
     return Circuit(h.value)
+
+
+def sv_fuse_density(gates, n: int, p: float, max_k: int) -> Circuit:
+    """The noisy circuit on the vectorised density matrix (2n qubits), fused."""
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    h = _vp()
+    _check(_lib.sv_fuse_density(ga.arr, ga.n, n, p, max_k, ctypes.byref(h)))
+    return Circuit(h.value)
+
+
+def sv_density_probs(s: State, out=None):
+    """Re rho[x, x] (float32 for C64, float64 for C128) of a vectorised density matrix."""
+    n2, dt, _ = sv_info(s)
+    if out is not None and hasattr(out, "data_ptr"):
+        _check(_lib.sv_density_probs(s.handle, int(out.data_ptr()), 1 if out.is_cuda else 0))
+        return out
+    a = out if out is not None else np.empty(1 << (n2 // 2), dtype=np.float32 if dt == SV_C64 else np.float64)
+    _check(_lib.sv_density_probs(s.handle, a.ctypes.data, 0))
+    return a
 
 
 def sv_fuse_like(pattern: Circuit, gates) -> Circuit:

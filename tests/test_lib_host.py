@@ -128,3 +128,25 @@ def test_fuse_like_equals_fuse(svlib):
                 assert ta == tb and np.array_equal(ua, ub)
     with pytest.raises(svlib.SvError):
         svlib.sv_fuse_like(pat, svlib.gates_from_specs(W.brickwork(9, 2)))
+
+
+def test_density_fusion_matches_density_oracle(svlib):
+    """sv_fuse_density's fused 2n-qubit schedule, applied by the state-vector oracle to
+    vec(|0><0|), gives vec(rho) of the density-matrix oracle (host only)."""
+    from oracle import density as D
+    rng = np.random.default_rng(77)
+    for n, p, k in ((2, 0.01, 2), (3, 0.05, 4), (4, 0.2, 5), (3, 0.0, 3), (4, 0.1, 0)):
+        specs = W.random_unitary_gates(n, 8, 2, rng) if n > 2 else W.bell()
+        c = svlib.sv_fuse_density(svlib.gates_from_specs(specs), n, p, k)
+        nf, n2 = svlib.sv_circuit_size(c)
+        assert n2 == 2 * n
+        v = oracle.basis(2 * n, 0)
+        for i in range(nf):
+            tg, u = svlib.sv_circuit_gate(c, i)
+            v = oracle.apply_gate(v, tg, u)
+        rho = D.run(n, OG.gate_list(specs), p)
+        assert np.max(np.abs(v - D.vec(rho))) < 1e-13, (n, p, k)
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse_density(svlib.gates_from_specs(W.bell()), 18, 0.01, 4)   # 2n > 34
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse_density(svlib.gates_from_specs(W.bell()), 2, 1.5, 4)
