@@ -67,3 +67,21 @@ def test_tc_norm_is_preserved_over_many_passes(gpu):
     assert np.max(np.abs(psi - ref)) < 1e-5
     assert 1 - abs(np.vdot(ref, psi)) ** 2 < 1e-6
     s.free()
+
+
+def test_tc_variants_edge_layouts(gpu):
+    """The width-5 kernel variants at their boundaries: one two-subtile tile (n = 13), the
+    one-subtile kernel at n = 12, width-4 gates widened to width 5, and the XOR member order
+    with one to four targets in the bank bits, against the oracle."""
+    sv = gpu
+    rng = np.random.default_rng(5150)
+    cases = [(13, (8, 9, 10, 11, 12)), (13, (0, 1, 2, 3, 4)), (13, (5, 6, 7, 8, 9)),
+             (12, (7, 8, 9, 10, 11)), (14, (0, 6, 9, 12, 13)), (14, (0, 1, 7, 10, 13)),
+             (14, (0, 1, 2, 10, 13)), (15, (1, 2, 3, 4, 14)),
+             (13, (9, 10, 11, 12)), (14, (0, 1, 2, 3)), (12, (4, 5, 6, 7))]
+    for n, tg in cases:
+        specs = W.random_unitary_gates(n, 2, len(tg), rng, exact_k=True, targets=tg)
+        psi0 = _state(n, rng)
+        ref = oracle.run(psi0.astype(np.complex128), OG.gate_list(specs))
+        got = _run(sv, n, psi0, sv.gates_from_specs(specs), 0)
+        assert np.max(np.abs(got - ref)) <= 1e-5, (n, tg)
