@@ -17,6 +17,8 @@ Contents (each function cites the passage it follows):
   prefix sums in a fixed order and SplitMix64 counters.
 * density.py   -- density matrices with single-qubit depolarizing noise after every gate
   (Section 9.5, Table 8).
+* structure.py -- control qubits and diagonal / monomial remainders of a gate matrix
+  (the structure the paper's fusion leaves unused, Sections 10-11).
 
 Parity status: apply, norm, probabilities, Pauli expectation, top-k, fusion and the
 precision rule are all pinned by tests under tests/test_oracle_*.py (closed forms,
@@ -33,7 +35,7 @@ from typing import Iterable, List, Sequence, Tuple
 
 import numpy as np
 
-from . import brute, density, fusion, gates, precision, sampling  # noqa: F401
+from . import brute, density, fusion, gates, precision, sampling, structure  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sv_oracle.c")
