@@ -163,7 +163,8 @@ typedef struct {
     double norm_before;         /* FP64 norms measured when adaptive (else 0) */
     double norm_after;
     double drift;               /* |norm_after - norm_before| of the reported run */
-    uint64_t bytes;             /* algorithmic HBM bytes of the passes: passes * 2 * 2^n * s */
+    uint64_t bytes;             /* algorithmic HBM bytes of the passes: 2 * 2^n * s per dense
+                                   pass, 2 * s per touched amplitude of a structured one */
     double apply_ms;            /* with opts->timing: CUDA-event time of all passes (ms) */
 } sv_apply_report;
 
@@ -226,10 +227,35 @@ sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64_t *out, in
  * descending, ties to the lower index.  idx/p are host arrays of k entries.  Synchronises. */
 sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
 
+/* ------------------------------------------------------ structure-aware application */
+
+/* The paper densifies every fused gate and names the structure it leaves unused among
+ * its limits and future work (Sections 10-11).  A gate's structure, exact on its FP64
+ * entries (no tolerance):
+ *   - local bit j is a CONTROL when U never changes bit j and U is the identity on the
+ *     half where bit j is 0;
+ *   - V = U restricted to "every control bit is 1", on the other targets, is
+ *     SV_STRUCT_DIAGONAL (off-diagonal entries all 0), SV_STRUCT_MONOMIAL (one nonzero in
+ *     every row and column: a permutation with phases) or SV_STRUCT_DENSE; a 1 x 1 V equal
+ *     to 1 is SV_STRUCT_IDENTITY (U = I).
+ * Every pass (sv_apply_gate, sv_apply_circuit) takes this structure into account unless
+ * SV_POLICY_DENSE_ONLY is set: amplitudes with a control bit 0 are neither read nor
+ * written, diagonal and monomial remainders cost one complex product per amplitude
+ * (none where the entry is exactly 1), and the identity launches nothing. */
+#define SV_STRUCT_DENSE 0u
+#define SV_STRUCT_DIAGONAL 1u
+#define SV_STRUCT_MONOMIAL 2u
+#define SV_STRUCT_IDENTITY 3u
+/* *kind = SV_STRUCT_* of V; *control_mask bit j set when targets[j] is a control (the
+ * caller's target order).  Either output may be NULL.  Host only. */
+sv_status sv_gate_structure(const sv_gate *g, uint32_t *kind, uint32_t *control_mask);
+
 /* Kernel selection flags for one state (default 0 = automatic: complex64 gates of width
- * 4 and 5 on states of at least k + 7 qubits run on the tensor cores, everything else on
- * the CUDA cores). */
+ * 4 and 5 on states of at least k + 7 qubits run on the tensor cores, complex128 gates of
+ * width <= 4 on states of at least 11 qubits too, structured gates on the structure-aware
+ * kernels, everything else on the CUDA cores). */
 #define SV_POLICY_NO_TENSOR_CORES 1u   /* always use the CUDA-core kernels */
+#define SV_POLICY_DENSE_ONLY 2u        /* ignore gate structure: every gate a dense pass */
 sv_status sv_set_policy(sv_state *s, uint32_t flags);
 
 /* ------------------------------------------------------------ batched execution */

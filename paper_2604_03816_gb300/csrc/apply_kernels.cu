@@ -180,9 +180,14 @@ sv_status launch_apply_t(sv_state *s, const svi::Gate &g) {
 
 namespace svi {
 
-sv_status launch_apply(sv_state *s, const Gate &g) {
+sv_status launch_apply(sv_state *s, const Gate &g, uint64_t *bytes) {
     if (g.k < 1 || g.k > SV_MAX_K || g.k > s->n)
         return set_error(SV_ERR_ARG, "apply: gate width out of range");
+    if (!(s->policy & SV_POLICY_DENSE_ONLY)) {
+        const Structure st = classify(g);
+        if (struct_preferred(s, st)) return launch_apply_struct(s, st, bytes);
+    }
+    if (bytes) *bytes = 2ull * ((s->dtype == SV_C64 ? 8ull : 16ull) << s->n);
     if (tc_eligible(s, g)) return launch_apply_tc(s, g);
     if (tc64_eligible(s, g)) return launch_apply_tc64(s, g);
     if (s->dtype == SV_C64) {

@@ -357,6 +357,21 @@ sv_status sv_choose_dtype(uint32_t n, uint64_t g, double eps_tol, sv_dtype *out,
     return SV_OK;
 }
 
+sv_status sv_gate_structure(const sv_gate *g, uint32_t *kind, uint32_t *control_mask) {
+    clear_error();
+    sv_status st = validate_gate(g, SV_MAX_QUBITS, "sv_gate_structure");
+    if (st != SV_OK) return st;
+    const Gate sg = sorted_gate(g->k, g->targets, g->u);
+    const Structure s = classify(sg);
+    uint32_t mask = 0;
+    for (uint32_t i = 0; i < s.nctrl; ++i)
+        for (uint32_t j = 0; j < g->k; ++j)
+            if (g->targets[j] == s.ctrl_q[i]) mask |= 1u << j;
+    if (kind) *kind = s.kind;
+    if (control_mask) *control_mask = mask;
+    return SV_OK;
+}
+
 sv_status sv_apply_gate(sv_state *s, const sv_gate *g) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_apply_gate: null state");
@@ -377,9 +392,12 @@ static sv_status run_schedule(sv_state *s, const sv_circuit *c, size_t begin, si
         SV_CUDA(cudaEventRecord(e0, s->stream));
     }
     sv_status st = SV_OK;
-    for (size_t i = begin; i < end && st == SV_OK; ++i) st = launch_apply(s, c->gates[i]);
+    for (size_t i = begin; i < end && st == SV_OK; ++i) {
+        uint64_t b = 0;
+        st = launch_apply(s, c->gates[i], &b);
+        r->bytes += b;
+    }
     r->passes += end - begin;
-    r->bytes += (uint64_t)(end - begin) * 2ull * ((uint64_t)elem_bytes(s->dtype) << s->n);
     if (timing) {
         cudaError_t e = cudaEventRecord(e1, s->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -568,7 +586,8 @@ sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
 sv_status sv_set_policy(sv_state *s, uint32_t flags) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_set_policy: null state");
-    if (flags & ~SV_POLICY_NO_TENSOR_CORES) return set_error(SV_ERR_ARG, "sv_set_policy: unknown flag");
+    if (flags & ~(SV_POLICY_NO_TENSOR_CORES | SV_POLICY_DENSE_ONLY))
+        return set_error(SV_ERR_ARG, "sv_set_policy: unknown flag");
     s->policy = flags;
     return SV_OK;
 }

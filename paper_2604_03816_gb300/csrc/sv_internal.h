@@ -28,6 +28,17 @@ struct Gate {
 // Relabel a gate's local bits so that its targets are ascending (same operator).
 Gate sorted_gate(uint32_t k, const uint32_t *targets, const double *u);
 
+// Exact structure of a sorted gate (structure.cpp): its control qubits and the reduced
+// gate V on the other targets (U = I except where every control bit is 1, V there).
+struct Structure {
+    uint32_t kind = SV_STRUCT_DENSE;   // of V: SV_STRUCT_*
+    uint32_t ctrl = 0;                 // local control bits of the gate
+    uint32_t nctrl = 0;
+    uint32_t ctrl_q[SV_MAX_K] = {0, 0, 0, 0, 0};   // their qubits, ascending
+    Gate v;                            // reduced gate (k = 0 for a 1 x 1 V)
+};
+Structure classify(const Gate &g);
+
 // The decisions of one run of Algorithm 2: contractions (u absorbs v) in order and the
 // final topological order of the surviving vertices.
 struct FusePlan {
@@ -101,7 +112,12 @@ struct sv_batch_launch {
 
 namespace svi {
 // ---- kernels (apply_kernels.cu / reduce_kernels.cu); all enqueue on s->stream ----
-sv_status launch_apply(sv_state *s, const Gate &g);
+// One pass of g; *bytes (if given) gets the pass's algorithmic HBM bytes: a full read and
+// write of the state, or of the amplitudes a structure-aware pass touches.
+sv_status launch_apply(sv_state *s, const Gate &g, uint64_t *bytes = nullptr);
+// Structure-aware pass (apply_struct.cu): is it preferred over the dense kernels, and run it.
+bool struct_preferred(const sv_state *s, const Structure &st);
+sv_status launch_apply_struct(sv_state *s, const Structure &st, uint64_t *bytes);
 bool tc_eligible(const sv_state *s, const Gate &g);        // apply_tc.cu
 sv_status launch_apply_tc(sv_state *s, const Gate &g);
 bool tc64_eligible(const sv_state *s, const Gate &g);      // apply_tc64.cu

@@ -35,12 +35,14 @@ EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
            "sv_expect_noalloc"]
-EXPORTS += ["sv_fuse_like", "sv_sample", "sv_fuse_density", "sv_density_probs"]
+EXPORTS += ["sv_fuse_like", "sv_sample", "sv_fuse_density", "sv_density_probs", "sv_gate_structure"]
 EXPORTS += ["sv_server_create", "sv_server_submit", "sv_server_poll", "sv_server_get_stats",
             "sv_server_destroy"]
 EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_get_state",
             "sv_batch_apply", "sv_batch_expect", "sv_batch_sync", "sv_batch_tune"]
 SV_POLICY_NO_TENSOR_CORES = 1
+SV_POLICY_DENSE_ONLY = 2
+SV_STRUCT_DENSE, SV_STRUCT_DIAGONAL, SV_STRUCT_MONOMIAL, SV_STRUCT_IDENTITY = 0, 1, 2, 3
 
 
 class SvError(RuntimeError):
@@ -126,6 +128,7 @@ _sig = {
     "sv_choose_dtype": [_u32, _u64, ctypes.c_double, ctypes.POINTER(_i32), _dp],
     "sv_apply_circuit": [_vp, _vp, ctypes.POINTER(sv_apply_opts), ctypes.POINTER(sv_apply_report)],
     "sv_apply_gate": [_vp, ctypes.POINTER(sv_gate)],
+    "sv_gate_structure": [ctypes.POINTER(sv_gate), ctypes.POINTER(_u32), ctypes.POINTER(_u32)],
     "sv_norm": [_vp, _dp],
     "sv_probs": [_vp, _vp, _i32],
     "sv_expect": [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp, ctypes.c_size_t, _dp],
@@ -389,6 +392,14 @@ def sv_apply_circuit(s: State, c: Circuit, adaptive: bool = False, drift_thresho
 def sv_apply_gate(s: State, targets: Sequence[int], u: np.ndarray) -> None:
     ga = GateArray([(targets, u)])
     _check(_lib.sv_apply_gate(s.handle, ga.arr))
+
+
+def sv_gate_structure(targets: Sequence[int], u: np.ndarray) -> Tuple[int, int]:
+    """(SV_STRUCT_* kind of the reduced gate, control mask over the caller's targets)."""
+    ga = GateArray([(targets, u)])
+    kind, mask = _u32(), _u32()
+    _check(_lib.sv_gate_structure(ga.arr, ctypes.byref(kind), ctypes.byref(mask)))
+    return kind.value, mask.value
 
 
 def sv_norm(s: State) -> float:

@@ -150,3 +150,54 @@ def test_density_fusion_matches_density_oracle(svlib):
         svlib.sv_fuse_density(svlib.gates_from_specs(W.bell()), 18, 0.01, 4)   # 2n > 34
     with pytest.raises(svlib.SvError):
         svlib.sv_fuse_density(svlib.gates_from_specs(W.bell()), 2, 1.5, 4)
+
+
+def _structured_gate(rng, k):
+    """A k-qubit gate I - P_C + P_C (V on the rest) with a random control set C and a
+    random diagonal / monomial / dense V (Kronecker construction, as in the oracle pins)."""
+    from oracle import brute
+    cmask = int(rng.integers(0, 1 << k))
+    ctl = [j for j in range(k) if (cmask >> j) & 1]
+    keep = [j for j in range(k) if j not in ctl]
+    d = 1 << len(keep)
+    ph = np.exp(1j * rng.uniform(0.1, 6.0, d))
+    kind = int(rng.integers(0, 3))
+    if kind == 0:
+        v = np.diag(ph)
+    elif kind == 1:
+        v = np.zeros((d, d), dtype=np.complex128)
+        v[np.arange(d), rng.permutation(d)] = ph
+    else:
+        z = rng.normal(size=(d, d)) + 1j * rng.normal(size=(d, d))
+        v = np.linalg.qr(z)[0]
+    proj = np.diag([0.0] * ((1 << len(ctl)) - 1) + [1.0]).astype(np.complex128)
+    P = brute.full_operator(k, ctl, proj) if ctl else np.eye(1 << k, dtype=np.complex128)
+    F = brute.full_operator(k, keep, v) if keep else v[0, 0] * np.eye(1 << k)
+    return np.eye(1 << k) - P + P @ F
+
+
+def test_gate_structure_matches_oracle(svlib):
+    """sv_gate_structure (controls in the caller's target order, the reduced gate's kind)
+    against oracle/structure.py on textbook gates, built structured gates with shuffled
+    targets, and the fused gates of QFT / brickwork circuits."""
+    from oracle import structure as OS
+    cases = [((0,), OG.matrix(g, p)) for g, p in [("x", ()), ("z", ()), ("h", ()), ("rz", (0.4,)),
+                                                    ("t", ()), ("i", ())]]
+    cases += [((3, 1), OG.matrix(g, p)) for g, p in [("cnot", ()), ("cz", ()), ("cp", (0.9,)),
+                                                       ("swap", ()), ("fsim", (0.3, 0.2))]]
+    cases.append(((5, 0, 2), OG.matrix("toffoli")))
+    rng = np.random.default_rng(17)
+    for _ in range(60):
+        k = int(rng.integers(1, 6))
+        tg = tuple(int(q) for q in rng.permutation(8)[:k])
+        cases.append((tg, _structured_gate(rng, k)))
+    for specs, n in [(W.qft(10), 10), (W.brickwork(8, 6, seed=3), 8)]:
+        for k in (2, 3, 5):
+            cases += [(tuple(t), u) for t, u in oracle.fuse(OG.gate_list(specs), n, k)]
+    kinds = set()
+    for tg, u in cases:
+        got = svlib.sv_gate_structure(tg, u)
+        assert got == OS.classify(tg, u), (tg, got)
+        kinds.add(got[0])
+    assert kinds == {svlib.SV_STRUCT_DENSE, svlib.SV_STRUCT_DIAGONAL, svlib.SV_STRUCT_MONOMIAL,
+                     svlib.SV_STRUCT_IDENTITY}
