@@ -67,42 +67,80 @@ __device__ __forceinline__ unsigned long long spread(unsigned long long x, const
 template <typename R>
 struct DiagArgs {
     R d[2 << SV_MAX_K];          // V's diagonal (re, im)
+    uint32_t one;                // bit r: entry r is exactly 1 in the state's precision
     void *psi;
-    unsigned long long count;    // amplitudes whose control bits are all 1
+    unsigned long long items;    // work items: VEC amplitudes each
     Spread sp;                   // the controls
     uint32_t k;                  // V's targets
     uint32_t t[SV_MAX_K];
 };
 
+template <typename R, int VEC> struct Vec;
+template <> struct Vec<float, 1> { using T = float2; };
+template <> struct Vec<float, 2> { using T = float4; };
+template <> struct Vec<double, 1> { using T = double2; };
+template <> struct Vec<double, 2> { using T = double4_16a; };
+
 template <typename R>
+__device__ __forceinline__ typename Cx<R>::T lane(const typename Vec<R, 1>::T &v, int) { return v; }
+template <typename R>
+__device__ __forceinline__ typename Cx<R>::T lane(const typename Vec<R, 2>::T &v, int q) {
+    return q ? mk(v.z, v.w) : mk(v.x, v.y);
+}
+__device__ __forceinline__ void set_lane(float2 &v, int, float2 c) { v = c; }
+__device__ __forceinline__ void set_lane(double2 &v, int, double2 c) { v = c; }
+__device__ __forceinline__ void set_lane(float4 &v, int q, float2 c) {
+    if (q) { v.z = c.x; v.w = c.y; } else { v.x = c.x; v.y = c.y; }
+}
+__device__ __forceinline__ void set_lane(double4_16a &v, int q, double2 c) {
+    if (q) { v.z = c.x; v.w = c.y; } else { v.x = c.x; v.y = c.y; }
+}
+
+// A work item is VEC consecutive amplitudes (no control below bit log2(VEC)), moved with
+// one vector access; it is skipped when all its entries are 1 and otherwise multiplied
+// whole (a product with exactly 1 returns the amplitude, up to the sign of a zero).
+template <typename R, int VEC>
 __global__ void __launch_bounds__(256) apply_diag(const __grid_constant__ DiagArgs<R> a) {
     using C = typename Cx<R>::T;
+    using V = typename Vec<R, VEC>::T;
     constexpr int ILP = 4;
     __shared__ C tab[1 << SV_MAX_K];
     if (threadIdx.x < (1u << a.k)) tab[threadIdx.x] = mk(a.d[2 * threadIdx.x], a.d[2 * threadIdx.x + 1]);
     __syncthreads();
-    C *psi = reinterpret_cast<C *>(a.psi);
+    V *psi = reinterpret_cast<V *>(a.psi);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long e0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e0 < a.count;
+    for (unsigned long long e0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e0 < a.items;
          e0 += ILP * stride) {
         unsigned long long idx[ILP];
-        C f[ILP], v[ILP];
+        uint32_t loc[ILP][VEC];
+        V v[ILP];
         bool act[ILP];
 #pragma unroll
         for (int u = 0; u < ILP; ++u) {
             const unsigned long long e = e0 + (unsigned long long)u * stride;
-            idx[u] = spread(e, a.sp);
-            uint32_t loc = 0;
+            const unsigned long long i0 = spread(e * VEC, a.sp);
+            idx[u] = i0 / VEC;
+            bool any = false;
 #pragma unroll
-            for (int j = 0; j < SV_MAX_K; ++j)
-                if (j < (int)a.k) loc |= (uint32_t)((idx[u] >> a.t[j]) & 1ull) << j;
-            f[u] = tab[loc];
-            act[u] = e < a.count && !(f[u].x == R(1) && f[u].y == R(0));
+            for (int q = 0; q < VEC; ++q) {
+                uint32_t l = 0;
+#pragma unroll
+                for (int j = 0; j < SV_MAX_K; ++j)
+                    if (j < (int)a.k) l |= (uint32_t)(((i0 + q) >> a.t[j]) & 1ull) << j;
+                loc[u][q] = l;
+                any |= !((a.one >> l) & 1u);
+            }
+            act[u] = e < a.items && any;
             if (act[u]) v[u] = psi[idx[u]];
         }
 #pragma unroll
-        for (int u = 0; u < ILP; ++u)
-            if (act[u]) psi[idx[u]] = cmul(f[u], v[u]);
+        for (int u = 0; u < ILP; ++u) {
+            if (!act[u]) continue;
+            V w = v[u];
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) set_lane(w, q, cmul(tab[loc[u][q]], lane<R>(v[u], q)));
+            psi[idx[u]] = w;
+        }
     }
 }
 
@@ -117,23 +155,39 @@ struct MonoArgs {
     Spread sp;                            // V's targets (0) and the controls (1)
 };
 
+// Groups in flight per thread: several for narrow V (more loads in flight per thread).
+template <typename R, int K>
+__host__ __device__ constexpr int mono_ilp() { return K <= 2 ? 4 : (K == 3 ? 2 : 1); }
+
 template <typename R, int K>
 __global__ void __launch_bounds__(256) apply_mono(const __grid_constant__ MonoArgs<R, K> a) {
     using C = typename Cx<R>::T;
-    constexpr int D = 1 << K;
+    constexpr int D = 1 << K, ILP = mono_ilp<R, K>();
     C *psi = reinterpret_cast<C *>(a.psi);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < a.count;
-         g += stride) {
-        const unsigned long long b = spread(g, a.sp);
-        C v[D];
+    for (unsigned long long g0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g0 < a.count;
+         g0 += ILP * stride) {
+        unsigned long long b[ILP];
+        C v[ILP][D];
 #pragma unroll
-        for (int r = 0; r < D; ++r)
-            if (!((a.skip >> r) & 1u)) v[r] = psi[b + a.soff[r]];
+        for (int u = 0; u < ILP; ++u) {
+            const unsigned long long g = g0 + (unsigned long long)u * stride;
+            b[u] = spread(g, a.sp);
+            if (g < a.count) {
 #pragma unroll
-        for (int r = 0; r < D; ++r) {
-            if ((a.skip >> r) & 1u) continue;
-            psi[b + a.off[r]] = ((a.plain >> r) & 1u) ? v[r] : cmul(mk(a.ph[2 * r], a.ph[2 * r + 1]), v[r]);
+                for (int r = 0; r < D; ++r)
+                    if (!((a.skip >> r) & 1u)) v[u][r] = psi[b[u] + a.soff[r]];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            if (g0 + (unsigned long long)u * stride >= a.count) continue;
+#pragma unroll
+            for (int r = 0; r < D; ++r) {
+                if ((a.skip >> r) & 1u) continue;
+                psi[b[u] + a.off[r]] =
+                    ((a.plain >> r) & 1u) ? v[u][r] : cmul(mk(a.ph[2 * r], a.ph[2 * r + 1]), v[u][r]);
+            }
         }
     }
 }
@@ -212,29 +266,39 @@ static bool is_one(const svi::cplx &z) {
     return static_cast<R>(z.real()) == R(1) && static_cast<R>(z.imag()) == R(0);
 }
 
+template <typename R, int VEC>
+static sv_status launch_diag_v(sv_state *s, const DiagArgs<R> &a) {
+    static int per_sm = 0;
+    const unsigned grid = grid_for(apply_diag<R, VEC>, &per_sm, s, (a.items + 3) / 4);
+    apply_diag<R, VEC><<<grid, 256, 0, s->stream>>>(a);
+    SV_CUDA(cudaGetLastError());
+    return SV_OK;
+}
+
 template <typename R>
 static sv_status launch_diag(sv_state *s, const svi::Structure &st, uint64_t *bytes) {
-    static int per_sm = 0;
     DiagArgs<R> a;
     const uint32_t dv = 1u << st.v.k;
     uint32_t changed = 0;
+    a.one = 0;
     for (uint32_t r = 0; r < dv; ++r) {
         const svi::cplx z = st.v.u[(size_t)r * dv + r];
         a.d[2 * r] = static_cast<R>(z.real());
         a.d[2 * r + 1] = static_cast<R>(z.imag());
-        changed += !is_one<R>(z);
+        if (is_one<R>(z)) a.one |= 1u << r;
+        else ++changed;
     }
+    const unsigned long long count = 1ull << (s->n - st.nctrl);   // controlled subspace
     a.psi = s->buf;
-    a.count = 1ull << (s->n - st.nctrl);
     a.sp = make_spread(st, false);
     a.k = st.v.k;
     for (uint32_t j = 0; j < SV_MAX_K; ++j) a.t[j] = j < st.v.k ? st.v.t[j] : 0u;
-    if (bytes) *bytes = 2ull * sizeof(R) * 2ull * (a.count >> st.v.k) * changed;
+    if (bytes) *bytes = 2ull * sizeof(R) * 2ull * (count >> st.v.k) * changed;
     if (changed == 0) return SV_OK;
-    const unsigned grid = grid_for(apply_diag<R>, &per_sm, s, (a.count + 3) / 4);
-    apply_diag<R><<<grid, 256, 0, s->stream>>>(a);
-    SV_CUDA(cudaGetLastError());
-    return SV_OK;
+    // pairs of amplitudes unless a control sits at bit 0 (or the subspace is one amplitude)
+    const bool pairs = count >= 2 && !(st.nctrl && st.ctrl_q[0] == 0);
+    a.items = pairs ? count / 2 : count;
+    return pairs ? launch_diag_v<R, 2>(s, a) : launch_diag_v<R, 1>(s, a);
 }
 
 template <typename R, int K>
@@ -268,7 +332,7 @@ static sv_status launch_mono(sv_state *s, const svi::Structure &st, uint64_t *by
     a.sp = make_spread(st, true);
     if (bytes) *bytes = 2ull * sizeof(R) * 2ull * a.count * moved;
     if (moved == 0) return SV_OK;
-    const unsigned grid = grid_for(apply_mono<R, K>, &per_sm, s, a.count);
+    const unsigned grid = grid_for(apply_mono<R, K>, &per_sm, s, (a.count + mono_ilp<R, K>() - 1) / mono_ilp<R, K>());
     apply_mono<R, K><<<grid, 256, 0, s->stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
