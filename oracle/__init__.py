@@ -191,6 +191,6 @@ def zz_chain_weight(n: int, k: np.ndarray) -> np.ndarray:
     return (n - 1) - 2 * pc
 
 
-def fuse(gate_list, n: int, qmax: int):
+def fuse(gate_list, n: int, qmax: int, commute: bool = False):
     """Algorithm 2 (see oracle/fusion.py)."""
-    return fusion.fuse(gate_list, n, qmax)
+    return fusion.fuse(gate_list, n, qmax, commute)

@@ -26,6 +26,22 @@ Readings where the paper is silent or ambiguous (each one is listed in the design doc
 * q_max^fuse = 0 means no fusion: the gates come back unchanged (targets sorted).
 
 The output is the list of surviving vertices in the same topological order.
+
+Commutation-aware variant (``commute=True``; the paper's fusion has no commutativity
+analysis and names it as future work, Sections 10-11):
+
+* Two gates commute when, on every qubit they share, both are diagonal in that qubit
+  (the gate's matrix never changes the qubit's bit) -- a sufficient condition.
+* DAG: for each qubit, scanning the gates in order, a gate that is not diagonal on it
+  gets an edge from every gate on it since (and including) the last such gate, and a
+  gate diagonal on it gets an edge from that last non-diagonal gate only.  Two gates
+  with no path between them then commute, so every topological order gives the same
+  product.
+* Fusion: Algorithm 2 as above; after v's predecessors, the sweep also tries the
+  vertices that share a qubit with v, are placed before v in the sweep's topological
+  order and are not its predecessors, in ascending id, contracting one when there is no
+  path from it to v (the two commute, so U_fused = U_v . U_u is the product in either
+  order).
 """
 from __future__ import annotations
 
@@ -135,20 +151,81 @@ class Dag:
         del self.preds[v], self.succs[v], self.q[v], self.u[v]
 
 
-def fuse(gates: Sequence[Tuple[Sequence[int], np.ndarray]], n: int, qmax: int
-         ) -> List[Tuple[Tuple[int, ...], np.ndarray]]:
-    """Algorithm 2.  Returns [(sorted targets, U)] in topological order."""
-    dag = Dag(gates, n)
+def diagonal_on(u: np.ndarray, j: int) -> bool:
+    """True when the matrix never changes local bit j: u[r][c] = 0 whenever bit j of r
+    differs from bit j of c."""
+    d = u.shape[0]
+    for r in range(d):
+        for c in range(d):
+            if ((r >> j) & 1) != ((c >> j) & 1) and u[r, c] != 0:
+                return False
+    return True
+
+
+class CommutingDag(Dag):
+    """The DAG of the commutation-aware variant (see the module docstring)."""
+
+    def __init__(self, gates: Sequence[Tuple[Sequence[int], np.ndarray]], n: int):
+        self.q, self.u, self.preds, self.succs = {}, {}, {}, {}
+        last_nondiag = [-1] * n
+        diag_since = [[] for _ in range(n)]   # gates diagonal on the qubit since then
+        for i, (tg, u) in enumerate(gates):
+            st, su = sort_targets(tuple(tg), np.asarray(u, dtype=np.complex128))
+            self.q[i], self.u[i] = st, su
+            self.preds[i], self.succs[i] = set(), set()
+            for j, qb in enumerate(st):
+                if diagonal_on(su, j):
+                    deps = [last_nondiag[qb]] if last_nondiag[qb] >= 0 else []
+                    diag_since[qb].append(i)
+                else:
+                    deps = list(diag_since[qb])
+                    if last_nondiag[qb] >= 0:
+                        deps.append(last_nondiag[qb])
+                    last_nondiag[qb] = i
+                    diag_since[qb] = []
+                for p in deps:
+                    self.preds[i].add(p)
+                    self.succs[p].add(i)
+
+    def any_path(self, u: int, v: int) -> bool:
+        """Is there a directed path u -> ... -> v?"""
+        stack = list(self.succs[u])
+        seen = set(stack)
+        while stack:
+            w = stack.pop()
+            if w == v:
+                return True
+            for x in self.succs[w]:
+                if x not in seen:
+                    seen.add(x)
+                    stack.append(x)
+        return False
+
+
+def fuse(gates: Sequence[Tuple[Sequence[int], np.ndarray]], n: int, qmax: int,
+         commute: bool = False) -> List[Tuple[Tuple[int, ...], np.ndarray]]:
+    """Algorithm 2 (commutation-aware with commute=True).  Returns [(sorted targets, U)]
+    in topological order."""
+    dag = CommutingDag(gates, n) if commute else Dag(gates, n)
     changed = qmax > 0
     while changed:
         changed = False
-        for v in dag.topo_order():
+        order = dag.topo_order()
+        pos = {v: i for i, v in enumerate(order)}
+        for v in order:
             if v not in dag.preds:            # absorbed earlier in this sweep
                 continue
-            for u in sorted(dag.preds[v]):
+            cands = sorted(dag.preds[v])
+            if commute:
+                cands += sorted(w for w in dag.preds if w != v and w not in dag.preds[v]
+                                and pos[w] < pos[v] and set(dag.q[w]) & set(dag.q[v]))
+            for u in cands:
                 if len(set(dag.q[u]) | set(dag.q[v])) > qmax:
                     continue
-                if dag.other_path(u, v):
+                if u in dag.preds[v]:
+                    if dag.other_path(u, v):
+                        continue
+                elif dag.any_path(u, v):
                     continue
                 dag.contract(u, v)
                 changed = True

@@ -124,3 +124,83 @@ def test_detour_check_is_load_bearing(monkeypatch):
     monkeypatch.setattr(fusion.Dag, "other_path", lambda self, u, v: False)
     with pytest.raises(AssertionError):
         oracle.fuse(gl, 6, 3)
+
+
+# ----------------------------------------------------------- commutation-aware variant
+
+def _diag_heavy(n, count, rng):
+    """Random circuits where most gates are diagonal (CZ, CP, RZ, T, Z) or controlled
+    (CNOT, Toffoli), with some dense ones (H, U3, random 2-qubit unitaries)."""
+    gl = []
+    for _ in range(count):
+        r = rng.random()
+        q = [int(x) for x in rng.choice(n, 3, replace=False)]
+        if r < 0.25:
+            gl.append(((q[0], q[1]), G.matrix("cp", (float(rng.uniform(0, 6)),))))
+        elif r < 0.33:
+            gl.append(((q[0],), G.matrix("rz", (float(rng.uniform(0, 6)),))))
+        elif r < 0.4:
+            gl.append(((q[0],), G.matrix(str(rng.choice(["t", "z"])))))
+        elif r < 0.5:
+            gl.append(((q[0], q[1]), G.matrix("cz")))
+        elif r < 0.65:
+            gl.append(((q[0], q[1]), G.matrix("cnot")))
+        elif r < 0.7:
+            gl.append(((q[0], q[1], q[2]), G.matrix("toffoli")))
+        elif r < 0.85:
+            gl.append(((q[0],), G.matrix("h")))
+        else:
+            gl.append(((q[0], q[1]), G.gate_list(W.random_unitary_gates(2, 1, 2, rng, exact_k=True,
+                                                                       targets=(0, 1)))[0][1]))
+    return gl
+
+
+def test_diagonal_on_qubit():
+    assert fusion.diagonal_on(G.matrix("cnot"), 0) and not fusion.diagonal_on(G.matrix("cnot"), 1)
+    assert fusion.diagonal_on(G.matrix("cz"), 0) and fusion.diagonal_on(G.matrix("cz"), 1)
+    assert not fusion.diagonal_on(G.matrix("swap"), 0) and not fusion.diagonal_on(G.H, 0)
+    assert fusion.diagonal_on(G.matrix("toffoli"), 1) and not fusion.diagonal_on(G.matrix("toffoli"), 2)
+
+
+def test_commuting_gates_fuse_around_a_blocker():
+    """CP(0,1), CP(1,2), CP(0,1)': Algorithm 2 keeps three gates at width 2 (the middle
+    gate separates the two CP(0,1) on qubit 1); all three commute, so the commutation-
+    aware variant fuses the outer two.  With an H on qubit 1 in between they no longer
+    commute and stay apart."""
+    a, b, c = (G.matrix("cp", (t,)) for t in (0.3, 0.5, 0.7))
+    gl = [((0, 1), a), ((1, 2), b), ((0, 1), c)]
+    assert len(oracle.fuse(gl, 3, 2)) == 3
+    f = oracle.fuse(gl, 3, 2, commute=True)
+    assert [t for t, _ in f] == [(0, 1), (1, 2)]
+    assert np.array_equal(np.diag(f[0][1]), np.diag(c @ a))
+    blocked = [((0, 1), a), ((1,), G.H), ((1, 2), b), ((0, 1), c)]
+    f2 = oracle.fuse(blocked, 3, 2, commute=True)
+    assert np.max(np.abs(_op(3, f2) - _op(3, blocked))) < 1e-13
+    assert not any(t == (0, 1) and np.allclose(u, c @ a) for t, u in f2)
+
+
+@pytest.mark.parametrize("qmax", [2, 3, 4, 5])
+@pytest.mark.parametrize("seed", range(4))
+def test_commutation_fused_equals_unfused(qmax, seed):
+    # Any topological order of the commutation DAG gives the same product (Eq. 10).
+    rng = np.random.default_rng(300 + 10 * qmax + seed)
+    n = 7
+    gl = _diag_heavy(n, 40, rng)
+    fused = oracle.fuse(gl, n, qmax, commute=True)
+    assert all(len(t) <= max(qmax, 3) for t, _ in fused)
+    assert np.max(np.abs(_op(n, fused) - _op(n, gl))) < 1e-12
+    assert len(fused) <= len(oracle.fuse(gl, n, qmax)) + 3
+
+
+def test_commutation_dag_edges_are_needed(monkeypatch):
+    # Planted mistake in the oracle: calling every gate diagonal on every qubit drops the
+    # edges that order H against the phases around it, and the fused product changes.
+    rng = np.random.default_rng(4)
+    dense = G.gate_list(W.random_unitary_gates(3, 1, 2, rng, exact_k=True, targets=(0, 2)))[0][1]
+    gl = [((0, 1), G.matrix("cp", (0.4,))), ((0, 2), dense), ((0, 1), G.matrix("cp", (1.1,)))]
+    good = oracle.fuse(gl, 3, 2, commute=True)
+    assert len(good) == 3
+    assert np.max(np.abs(_op(3, good) - _op(3, gl))) < 1e-13
+    monkeypatch.setattr(fusion, "diagonal_on", lambda u, j: True)
+    bad = oracle.fuse(gl, 3, 2, commute=True)
+    assert np.max(np.abs(_op(3, bad) - _op(3, gl))) > 0.1
