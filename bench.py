@@ -82,6 +82,8 @@ def parse():
                          "qft: QFT of a basis state with structure-aware passes against "
                          "the same schedule forced dense")
     ap.add_argument("--shots", type=int, default=1 << 20, help="sample: shots per step")
+    ap.add_argument("--circuit", default="qft", choices=["qft", "phase_heavy", "qaoa"],
+                    help="qft mode: the circuit family (QFT; random diagonal-heavy; QAOA layers)")
     ap.add_argument("--p-depol", type=float, default=0.01, help="noise: depolarizing p")
     ap.add_argument("--noise-n", type=int, default=15, help="noise: qubits of the density matrix")
     ap.add_argument("--count", type=int, default=512, help="batched: number of circuits")
@@ -361,11 +363,13 @@ def run_noise(args):
 
 
 def run_qft(args):
-    """QFT of a seeded basis state (the QFT family of Tables 4 and 7), fused at --k: most
-    fused gates are diagonal products of controlled phases with a control qubit, so the
-    structure-aware passes touch half of the state or less.  One step = sv_fuse +
-    sv_set_basis + sv_apply_circuit + sv_norm; the same steps with SV_POLICY_DENSE_ONLY
-    are timed beside it."""
+    """Structure-aware passes and commutation-aware fusion on circuits with diagonal and
+    controlled gates: QFT of a seeded basis state (the QFT family of Tables 4 and 7;
+    default), a random diagonal-heavy circuit, or QAOA layers.  One step = sv_fuse_ex +
+    sv_set_basis + sv_apply_circuit + sv_norm.  Three variants are timed: the paper's
+    fusion with every pass dense (SV_POLICY_DENSE_ONLY), the same schedule with the
+    structure-aware passes, and commutation-aware fusion (SV_FUSE_COMMUTE) with the
+    structure-aware passes; the line's value is the best of the last two."""
     import torch
     from paper_2604_03816_gb300 import sv
     torch.cuda.set_device(0)
@@ -375,16 +379,23 @@ def run_qft(args):
     # complex128 gates of width 5 have no tensor-core pass: fuse complex128 at k <= 4
     k = args.k if dt == sv.SV_C64 else min(args.k, 4)
     x = int(np.random.default_rng(W.seed_for(6, n)).integers(0, 1 << n))
-    specs = W.qft(n)
+    if args.circuit == "qft":
+        specs, what = W.qft(n), "QFT (H + controlled phases + final swaps) of a seeded basis state"
+    elif args.circuit == "phase_heavy":
+        specs, what = W.phase_heavy(n, 16 * n), f"random diagonal-heavy circuit ({16 * n} gates) on a seeded basis state"
+    else:
+        specs, what = W.qaoa(n, 3, 3 * n), f"QAOA, 3 layers of {3 * n} ZZ phases + RX, on a seeded basis state"
     gates = sv.gates_from_specs(specs)
     state = sv.sv_alloc(n, dt, stream=stream)
     res = {}
+    variants = (("dense", sv.SV_POLICY_DENSE_ONLY, 0), ("structure", 0, 0),
+                ("structure+commute", 0, sv.SV_FUSE_COMMUTE))
     with torch.cuda.stream(stream):
-        for policy in (sv.SV_POLICY_DENSE_ONLY, 0):
+        for name, policy, flags in variants:
             sv.sv_set_policy(state, policy)
 
             def step(timing=False):
-                c = sv.sv_fuse(gates, n, k)
+                c = sv.sv_fuse_ex(gates, n, k, flags)
                 sv.sv_set_basis(state, x)
                 rep = sv.sv_apply_circuit(state, c, timing=timing)
                 return rep, sv.sv_norm(state), len(c)
@@ -400,25 +411,27 @@ def run_qft(args):
                     reps.append(rep)
                 e1.record(stream)
                 torch.cuda.synchronize()
-            res[policy] = (e0.elapsed_time(e1) / args.steps, reps, norm, nfused, clk.summary())
+            res[name] = (e0.elapsed_time(e1) / args.steps, reps, norm, nfused, clk.summary())
     state.free()
-    ms, reps, norm, nfused, clocks = res[0]
-    dense_ms = res[sv.SV_POLICY_DENSE_ONLY][0]
+    best = min(("structure", "structure+commute"), key=lambda v: res[v][0])
+    ms, reps, norm, nfused, clocks = res[best]
+    dense_ms = res["dense"][0]
     apply_ms = sum(r["apply_ms"] for r in reps)
     abytes = sum(r["bytes"] for r in reps)
-    dense_bytes = reps[-1]["passes"] * 2 * ((8 if dt == sv.SV_C64 else 16) << n)
+    dense_bytes = res["dense"][1][-1]["passes"] * 2 * ((8 if dt == sv.SV_C64 else 16) << n)
     achieved = abytes / (apply_ms / 1000.0) / 1e9
     peak, peak_kind = hbm_peak()
-    out = {"metric": "QFT circuits/s (structure-aware passes)", "value": 1000.0 / ms,
+    out = {"metric": f"{args.circuit} circuits/s (structure-aware passes)", "value": 1000.0 / ms,
            "unit": "circuits/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if dt == sv.SV_C64 else "f64", "data": "synthetic",
-           "config": {"workload": f"QFT {n}q (H + controlled phases + final swaps) of a seeded "
-                                  f"basis state, {args.dtype}, DAG fusion k={k}",
+           "config": {"workload": f"{what}, {n}q, {args.dtype}, DAG fusion k={k}, {best}",
                       "gates": len(specs), "fused_gates": nfused, "x": x,
                       "state_bytes": (8 if dt == sv.SV_C64 else 16) << n,
                       "l2": "state larger than L2, no flush needed"},
-           "dense_only_ms_per_step": dense_ms, "speedup_vs_dense": dense_ms / ms,
+           "variants_ms_per_step": {v: res[v][0] for v in res},
+           "variants_fused_gates": {v: res[v][3] for v in res},
+           "speedup_vs_dense": dense_ms / ms,
            "algorithmic_bytes_per_step": abytes / len(reps),
            "dense_bytes_per_step": dense_bytes, "norm": norm,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

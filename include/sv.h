@@ -127,9 +127,21 @@ sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device);
  * Copies the matrices; free the result with sv_circuit_free.  Host only. */
 sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k,
                   sv_circuit **out);
+/* sv_fuse with flags.  SV_FUSE_COMMUTE: commutation-aware fusion (the paper's fusion does
+ * no commutativity analysis; Sections 10-11 name it as future work).  Two gates commute
+ * when, on every qubit they share, both are diagonal in that qubit (neither changes its
+ * bit; exact test on the FP64 entries).  The DAG keeps, per qubit, the edges from a gate
+ * not diagonal on it to every gate on it since the previous such gate and from that gate
+ * to the diagonal ones after it; the sweeps also contract, after v's predecessors, the
+ * vertices that share a qubit with v, are placed before it and have no path to it
+ * (ascending id).  Deterministic.  flags = 0 is sv_fuse.  SV_ERR_ARG for unknown flags. */
+#define SV_FUSE_COMMUTE 1u
+sv_status sv_fuse_ex(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k, uint32_t flags,
+                     sv_circuit **out);
 /* Fuse `gates` with the decisions sv_fuse made for `pattern` (the gates must act on the
- * same qubits, gate by gate, as the ones `pattern` was fused from; matrices may differ --
- * a parameter sweep).  Algorithm 2's decisions depend only on the qubit sets, so the
+ * same qubits, gate by gate, as the ones `pattern` was fused from, and for a pattern
+ * fused with SV_FUSE_COMMUTE be diagonal on the same qubits; matrices may differ -- a
+ * parameter sweep).  Algorithm 2's decisions depend only on the qubit sets, so the
  * result equals sv_fuse(gates, n, max_k) bit for bit, without repeating the DAG search.
  * SV_ERR_ARG if the qubits differ.  Host only. */
 sv_status sv_fuse_like(const sv_circuit *pattern, const sv_gate *gates, size_t ngates,

@@ -13,6 +13,15 @@
 // through other qubits).  u absorbs v: U_u <- E(U_v) . E(U_u) on the sorted union of
 // their qubits (E = embedding with identities), v's in- and out-edges move to u, and u
 // keeps its id.  The final schedule lists the survivors in the same topological order.
+//
+// Commutation-aware variant (the paper's fusion does no commutativity analysis and
+// names it as future work, Sections 10-11): two gates commute when both are diagonal in
+// every qubit they share (neither changes that qubit's bit).  Per qubit, a gate that is
+// not diagonal on it depends on every gate on it since the previous such gate, a gate
+// diagonal on it only on that previous gate; vertices with no path between them then
+// commute.  The sweep also tries, after v's predecessors, the vertices that share a
+// qubit with v, are placed before v and are not its predecessors (ascending id), and
+// contracts one with no path to v (either product order is the same operator).
 #include <algorithm>
 #include <queue>
 #include <set>
@@ -108,20 +117,46 @@ Gate fused_product(const Gate &gu, const Gate &gv, const uint32_t *qs, uint32_t 
 
 class Dag {
   public:
-    Dag(const std::vector<Gate> &gates, uint32_t n)
-        : nodes_(gates.size()), seen_(gates.size(), 0), pos_(gates.size(), 0) {
+    Dag(const std::vector<Gate> &gates, uint32_t n, bool commute)
+        : nodes_(gates.size()), seen_(gates.size(), 0), pos_(gates.size(), 0), on_qubit_(n) {
         std::vector<int> last(n, -1);
+        std::vector<std::vector<int>> diag_since(commute ? n : 0);
         for (size_t i = 0; i < gates.size(); ++i) {
             nodes_[i].g = gates[i];
+            const uint32_t dmask = commute ? diagonal_mask(gates[i]) : 0u;
             for (uint32_t j = 0; j < gates[i].k; ++j) {
                 const uint32_t q = gates[i].t[j];
-                if (last[q] >= 0) {
-                    nodes_[i].preds.insert(last[q]);
-                    nodes_[last[q]].succs.insert((int)i);
+                on_qubit_[q].insert((int)i);
+                if (!commute) {
+                    if (last[q] >= 0) edge(last[q], (int)i);
+                    last[q] = (int)i;
+                } else if ((dmask >> j) & 1u) {
+                    if (last[q] >= 0) edge(last[q], (int)i);
+                    diag_since[q].push_back((int)i);
+                } else {
+                    for (int w : diag_since[q]) edge(w, (int)i);
+                    if (last[q] >= 0) edge(last[q], (int)i);
+                    diag_since[q].clear();
+                    last[q] = (int)i;
                 }
-                last[q] = (int)i;
             }
         }
+    }
+
+    void edge(int u, int v) {
+        nodes_[v].preds.insert(u);
+        nodes_[u].succs.insert(v);
+    }
+
+    // Alive vertices that share a qubit with v, are placed before it in the sweep's
+    // order and are not its predecessors, in ascending id.
+    std::vector<int> siblings(int v) const {
+        std::set<int> out;
+        const Node &V = nodes_[v];
+        for (uint32_t j = 0; j < V.g.k; ++j)
+            for (int w : on_qubit_[V.g.t[j]])
+                if (w != v && pos_[w] < pos_[v] && !V.preds.count(w)) out.insert(w);
+        return std::vector<int>(out.begin(), out.end());
     }
 
     std::vector<int> topo_order() const {
@@ -185,6 +220,8 @@ class Dag {
 
     void contract(int u, int v, const uint32_t *qs, uint32_t m) {
         Node &U = nodes_[u], &V = nodes_[v];
+        for (uint32_t j = 0; j < V.g.k; ++j) on_qubit_[V.g.t[j]].erase(v);
+        for (uint32_t j = 0; j < m; ++j) on_qubit_[qs[j]].insert(u);
         U.g = fused_product(U.g, V.g, qs, m);
         for (int w : V.preds)
             if (w != u) {
@@ -207,13 +244,31 @@ class Dag {
     std::vector<Node> nodes_;
     std::vector<uint32_t> seen_;
     std::vector<int> pos_, stack_;
+    std::vector<std::set<int>> on_qubit_;   // alive vertices acting on each qubit
     uint32_t stamp_ = 0;
 };
 
 }  // namespace
 
-std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k, FusePlan *plan) {
-    Dag dag(in, n);
+uint32_t diagonal_mask(const Gate &g) {
+    const uint32_t d = 1u << g.k;
+    uint32_t mask = 0;
+    for (uint32_t j = 0; j < g.k; ++j) {
+        bool diag = true;
+        for (uint32_t r = 0; r < d && diag; ++r)
+            for (uint32_t c = 0; c < d; ++c)
+                if (((r ^ c) >> j) & 1u && g.u[(size_t)r * d + c] != cplx(0.0, 0.0)) {
+                    diag = false;
+                    break;
+                }
+        if (diag) mask |= 1u << j;
+    }
+    return mask;
+}
+
+std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k, FusePlan *plan,
+                             bool commute) {
+    Dag dag(in, n, commute);
     if (plan) plan->contractions.clear();
     bool changed = max_k > 0;
     while (changed) {
@@ -222,8 +277,12 @@ std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t m
         dag.set_positions(order);
         for (int v : order) {
             if (!dag.nodes_[v].alive) continue;
-            const std::vector<int> preds(dag.nodes_[v].preds.begin(), dag.nodes_[v].preds.end());
-            for (int u : preds) {
+            std::vector<int> cands(dag.nodes_[v].preds.begin(), dag.nodes_[v].preds.end());
+            if (commute) {
+                const std::vector<int> sib = dag.siblings(v);
+                cands.insert(cands.end(), sib.begin(), sib.end());
+            }
+            for (int u : cands) {
                 uint32_t qs[2 * SV_MAX_K];
                 const uint32_t m = Dag::union_qubits(dag.nodes_[u].g, dag.nodes_[v].g, qs);
                 if (m > max_k) continue;

@@ -195,19 +195,21 @@ sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device) {
 
 // A circuit object holding Algorithm 2's schedule of `in` and what sv_fuse_like needs.
 static sv_status make_circuit(const std::vector<Gate> &in, uint32_t n, uint32_t max_k, sv_circuit **out,
-                              const char *who) {
+                              const char *who, uint32_t flags = 0) {
     sv_circuit *c = new (std::nothrow) sv_circuit();
     if (!c) return set_error(SV_ERR_OOM, std::string(who) + ": host allocation failed");
     c->n = n;
     try {
         c->max_k = max_k;
+        c->flags = flags;
         c->in_k.reserve(in.size());
         c->in_t.reserve(in.size() * SV_MAX_K);
         for (const Gate &g : in) {
             c->in_k.push_back(g.k);
             for (uint32_t j = 0; j < SV_MAX_K; ++j) c->in_t.push_back(j < g.k ? g.t[j] : 0);
+            if (flags & SV_FUSE_COMMUTE) c->in_diag.push_back(diagonal_mask(g));
         }
-        c->gates = fuse_gates(in, n, max_k, &c->plan);
+        c->gates = fuse_gates(in, n, max_k, &c->plan, (flags & SV_FUSE_COMMUTE) != 0);
     } catch (const std::bad_alloc &) {
         delete c;
         return set_error(SV_ERR_OOM, std::string(who) + ": host allocation failed");
@@ -218,11 +220,17 @@ static sv_status make_circuit(const std::vector<Gate> &in, uint32_t n, uint32_t 
 
 sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k,
                   sv_circuit **out) {
+    return sv_fuse_ex(gates, ngates, n, max_k, 0, out);
+}
+
+sv_status sv_fuse_ex(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_k, uint32_t flags,
+                     sv_circuit **out) {
     clear_error();
     if (!out) return set_error(SV_ERR_ARG, "sv_fuse: null out");
     *out = nullptr;
     if (n < 1 || n > SV_MAX_QUBITS) return set_error(SV_ERR_ARG, "sv_fuse: n must be 1..34");
     if (max_k > SV_MAX_K) return set_error(SV_ERR_ARG, "sv_fuse: max_k must be 0..5");
+    if (flags & ~SV_FUSE_COMMUTE) return set_error(SV_ERR_ARG, "sv_fuse_ex: unknown flag");
     if (ngates && !gates) return set_error(SV_ERR_ARG, "sv_fuse: null gates");
     std::vector<Gate> in;
     in.reserve(ngates);
@@ -231,7 +239,7 @@ sv_status sv_fuse(const sv_gate *gates, size_t ngates, uint32_t n, uint32_t max_
         if (st != SV_OK) return set_error(st, sv_last_error() + (" (gate " + std::to_string(i) + ")"));
         in.push_back(sorted_gate(gates[i].k, gates[i].targets, gates[i].u));
     }
-    return make_circuit(in, n, max_k, out, "sv_fuse");
+    return make_circuit(in, n, max_k, out, "sv_fuse", flags);
 }
 
 // Density matrices with single-qubit depolarizing noise (Section 9.5): rho on n qubits as
@@ -302,14 +310,20 @@ sv_status sv_fuse_like(const sv_circuit *pattern, const sv_gate *gates, size_t n
         if (!same)
             return set_error(SV_ERR_ARG, "sv_fuse_like: gate " + std::to_string(i) +
                                              " acts on other qubits than the pattern's");
+        if ((pattern->flags & SV_FUSE_COMMUTE) && diagonal_mask(g) != pattern->in_diag[i])
+            return set_error(SV_ERR_ARG, "sv_fuse_like: gate " + std::to_string(i) +
+                                             " commutes differently from the pattern's (its "
+                                             "diagonal qubits differ)");
     }
     sv_circuit *c = new (std::nothrow) sv_circuit();
     if (!c) return set_error(SV_ERR_OOM, "sv_fuse_like: host allocation failed");
     try {
         c->n = pattern->n;
         c->max_k = pattern->max_k;
+        c->flags = pattern->flags;
         c->in_k = pattern->in_k;
         c->in_t = pattern->in_t;
+        c->in_diag = pattern->in_diag;
         c->plan = pattern->plan;
         c->gates = replay_fusion(std::move(in), pattern->plan);
     } catch (const std::bad_alloc &) {

@@ -46,9 +46,12 @@ struct FusePlan {
     std::vector<int> order;
 };
 
-// Algorithm 2 over sorted gates (fuse.cpp); records its decisions in *plan if given.
+// Algorithm 2 over sorted gates (fuse.cpp); records its decisions in *plan if given;
+// commute: the commutation-aware DAG and contractions of commuting vertices.
 std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t max_k,
-                             FusePlan *plan = nullptr);
+                             FusePlan *plan = nullptr, bool commute = false);
+// Bit j set when the gate never changes its local bit j (fuse.cpp).
+uint32_t diagonal_mask(const Gate &g);
 // g as an m-qubit gate U (x) I (m >= g.k, m <= n; fuse.cpp).
 Gate widen_gate(const Gate &g, uint32_t n, uint32_t m);
 // Apply a recorded plan to gates with the same qubit sets (fuse.cpp).
@@ -61,8 +64,10 @@ struct sv_circuit {
     std::vector<svi::Gate> gates;
     // how it was fused, for sv_fuse_like: input qubit sets and the recorded plan
     uint32_t max_k = 0;
+    uint32_t flags = 0;               // SV_FUSE_* it was fused with
     std::vector<uint32_t> in_k;
     std::vector<uint32_t> in_t;       // SV_MAX_K per input gate, sorted
+    std::vector<uint32_t> in_diag;    // with SV_FUSE_COMMUTE: diagonal_mask of each input gate
     svi::FusePlan plan;
 };
 

@@ -35,13 +35,15 @@ EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
            "sv_expect_noalloc"]
-EXPORTS += ["sv_fuse_like", "sv_sample", "sv_fuse_density", "sv_density_probs", "sv_gate_structure"]
+EXPORTS += ["sv_fuse_like", "sv_sample", "sv_fuse_density", "sv_density_probs", "sv_gate_structure",
+            "sv_fuse_ex"]
 EXPORTS += ["sv_server_create", "sv_server_submit", "sv_server_poll", "sv_server_get_stats",
             "sv_server_destroy"]
 EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_get_state",
             "sv_batch_apply", "sv_batch_expect", "sv_batch_sync", "sv_batch_tune"]
 SV_POLICY_NO_TENSOR_CORES = 1
 SV_POLICY_DENSE_ONLY = 2
+SV_FUSE_COMMUTE = 1
 SV_STRUCT_DENSE, SV_STRUCT_DIAGONAL, SV_STRUCT_MONOMIAL, SV_STRUCT_IDENTITY = 0, 1, 2, 3
 
 
@@ -119,6 +121,7 @@ _sig = {
     "sv_set_state": [_vp, _vp, _i32],
     "sv_get_state": [_vp, _vp, _i32],
     "sv_fuse": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32, ctypes.POINTER(_vp)],
+    "sv_fuse_ex": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32, _u32, ctypes.POINTER(_vp)],
     "sv_fuse_density": [ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, ctypes.c_double, _u32,
                         ctypes.POINTER(_vp)],
     "sv_circuit_free": [_vp],
@@ -236,6 +239,14 @@ def sv_fuse(gates, n: int, max_k: int) -> Circuit:
     ga = gates if isinstance(gates, GateArray) else GateArray(gates)
     h = _vp()
     _check(_lib.sv_fuse(ga.arr, ga.n, n, max_k, ctypes.byref(h)))
+    return Circuit(h.value)
+
+
+def sv_fuse_ex(gates, n: int, max_k: int, flags: int = 0) -> Circuit:
+    """sv_fuse with SV_FUSE_* flags (SV_FUSE_COMMUTE: commutation-aware fusion)."""
+    ga = gates if isinstance(gates, GateArray) else GateArray(gates)
+    h = _vp()
+    _check(_lib.sv_fuse_ex(ga.arr, ga.n, n, max_k, flags, ctypes.byref(h)))
     return Circuit(h.value)
 
 

@@ -181,3 +181,22 @@ def test_qft_30q_closed_form_sampled(gpu, dtype):
     s.free()
     del buf
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("k", [3, 5])
+def test_commutation_fused_circuits(gpu, dtype, k):
+    """Circuits fused with SV_FUSE_COMMUTE (reordered commuting gates) run on the
+    structure-aware passes: the state equals the oracle's unfused one."""
+    sv = gpu
+    for specs, n in ((W.phase_heavy(16, 200, seed=21), 16), (W.qaoa(15, 3, 30, seed=22), 15),
+                     (W.qft(14), 14)):
+        x = 0x1234 & ((1 << n) - 1)
+        ref = oracle.simulate(n, specs, x)
+        c = sv.sv_fuse_ex(sv.gates_from_specs(specs), n, k, sv.SV_FUSE_COMMUTE)
+        s = sv.sv_alloc(n, dtype, stream=_torch().cuda.current_stream())
+        sv.sv_set_basis(s, x)
+        sv.sv_apply_circuit(s, c)
+        psi = sv.sv_get_state(s).astype(np.complex128)
+        s.free()
+        assert float(np.max(np.abs(psi - ref))) <= TOL[dtype]

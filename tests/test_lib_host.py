@@ -201,3 +201,42 @@ def test_gate_structure_matches_oracle(svlib):
         kinds.add(got[0])
     assert kinds == {svlib.SV_STRUCT_DENSE, svlib.SV_STRUCT_DIAGONAL, svlib.SV_STRUCT_MONOMIAL,
                      svlib.SV_STRUCT_IDENTITY}
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_commutation_fusion_matches_oracle(svlib, k):
+    """sv_fuse_ex(SV_FUSE_COMMUTE): the schedule (targets, in order) bit-exact against
+    the oracle's commutation-aware Algorithm 2, the products to 1e-12."""
+    cases = [(W.phase_heavy(7, 60, seed=k), 7), (W.qft(10), 10), (W.qaoa(9, 2, 14, seed=k), 9),
+             (W.brickwork(8, 6, seed=3), 8), (W.hea(8, 2, seed=4), 8)]
+    for specs, n in cases:
+        want = oracle.fuse(OG.gate_list(specs), n, k, commute=True)
+        c = svlib.sv_fuse_ex(svlib.gates_from_specs(specs), n, k, svlib.SV_FUSE_COMMUTE)
+        assert len(c) == len(want)
+        for i, (tw, uw) in enumerate(want):
+            tg, ug = svlib.sv_circuit_gate(c, i)
+            assert tg == tuple(tw), (i, tg, tw)
+            assert np.max(np.abs(ug - uw)) < 1e-12
+
+
+def test_commutation_fuse_like_checks_structure(svlib):
+    n = 6
+    specs = W.phase_heavy(n, 40, seed=11)
+    pattern = svlib.sv_fuse_ex(svlib.gates_from_specs(specs), n, 3, svlib.SV_FUSE_COMMUTE)
+    # a parameter sweep that keeps every gate's diagonal qubits replays exactly
+    sweep = [s if s.name not in ("cp", "rz") else W.GateSpec(s.name, s.qubits, (s.params[0] + 0.5,))
+             for s in specs]
+    direct = svlib.sv_fuse_ex(svlib.gates_from_specs(sweep), n, 3, svlib.SV_FUSE_COMMUTE)
+    like = svlib.sv_fuse_like(pattern, svlib.gates_from_specs(sweep))
+    assert len(like) == len(direct)
+    for i in range(len(direct)):
+        a, b = svlib.sv_circuit_gate(like, i), svlib.sv_circuit_gate(direct, i)
+        assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    # a CZ turned into a CNOT on the same qubits commutes differently: refused
+    i = next(j for j, s in enumerate(specs) if s.name == "cz")
+    changed = list(specs)
+    changed[i] = W.GateSpec("cnot", specs[i].qubits)
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse_like(pattern, svlib.gates_from_specs(changed))
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse_ex(svlib.gates_from_specs(specs), n, 3, 2)

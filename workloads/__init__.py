@@ -236,6 +236,59 @@ def random_unitary_gates(n: int, count: int, kmax: int, rng: np.random.Generator
     return gates
 
 
+def phase_heavy(n: int, count: int, seed: Optional[int] = None) -> List[GateSpec]:
+    """Random circuits dominated by diagonal and controlled gates (CP, RZ, T, Z, CZ, CNOT,
+    Toffoli) with some dense ones (H, random 2-qubit unitaries), on random qubits: inputs
+    where commutation and gate structure matter."""
+    rng = np.random.default_rng(seed_for(7, n) if seed is None else seed)
+    gates: List[GateSpec] = []
+    for _ in range(count):
+        r = rng.random()
+        q = tuple(int(x) for x in rng.choice(n, size=min(3, n), replace=False))
+        if r < 0.25 and n >= 2:
+            gates.append(GateSpec("cp", q[:2], (float(rng.uniform(0, 2 * math.pi)),)))
+        elif r < 0.33:
+            gates.append(GateSpec("rz", q[:1], (float(rng.uniform(0, 2 * math.pi)),)))
+        elif r < 0.4:
+            gates.append(GateSpec(str(rng.choice(["t", "z"])), q[:1]))
+        elif r < 0.5 and n >= 2:
+            gates.append(GateSpec("cz", q[:2]))
+        elif r < 0.65 and n >= 2:
+            gates.append(GateSpec("cnot", q[:2]))
+        elif r < 0.7 and n >= 3:
+            gates.append(GateSpec("toffoli", q[:3]))
+        elif r < 0.85 or n < 2:
+            gates.append(GateSpec("h", q[:1]))
+        else:
+            gates.append(GateSpec("unitary", q[:2], (), False, haar_unitary(4, rng)))
+    return gates
+
+
+def qaoa(n: int, layers: int = 3, edges: int = 24, seed: Optional[int] = None) -> List[GateSpec]:
+    """QAOA-style layers: exp(-i gamma Z_a Z_b) on `edges` random pairs in random order
+    (diag(e^{-i g}, e^{i g}, e^{i g}, e^{-i g})), then RX(beta) on every qubit."""
+    rng = np.random.default_rng(seed_for(8, n) if seed is None else seed)
+    gates: List[GateSpec] = []
+    for _ in range(layers):
+        g = float(rng.uniform(0, math.pi))
+        pairs = set()
+        while len(pairs) < min(edges, n * (n - 1) // 2):
+            a, b = (int(x) for x in rng.choice(n, size=2, replace=False))
+            pairs.add((min(a, b), max(a, b)))
+        order = sorted(pairs)
+        rng.shuffle(order)
+        zz = (complex(math.cos(g), -math.sin(g)), 0j, 0j, 0j,
+              0j, complex(math.cos(g), math.sin(g)), 0j, 0j,
+              0j, 0j, complex(math.cos(g), math.sin(g)), 0j,
+              0j, 0j, 0j, complex(math.cos(g), -math.sin(g)))
+        for a, b in order:
+            gates.append(GateSpec("unitary", (a, b), (), False, zz))
+        beta = float(rng.uniform(0, math.pi))
+        for q in range(n):
+            gates.append(GateSpec("rx", (q,), (beta,)))
+    return gates
+
+
 @dataclass
 class Request:
     arrival_s: float
