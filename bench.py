@@ -525,12 +525,14 @@ def run_batched(args):
     with torch.cuda.stream(stream):
         for w in widths:
             batches[w] = sv.sv_batch_alloc(w, sv.SV_C64, len(groups[w]), stream=stream)
-            tune[w] = sv.sv_batch_tune(batches[w], gates[w][0], 1, 4)
+            tune[w] = sv.sv_batch_tune(batches[w], gates[w][0], 1, 5)
 
         def step():
             fuse_s = 0.0
             out = {}
-            for w in widths:
+            # widest first: its passes (most of the GPU time) overlap the host work
+            # (fusion, matrix tables) of the narrower ones
+            for w in sorted(widths, reverse=True):
                 t0 = time.perf_counter()
                 # Algorithm 2 once per width; the other circuits of the family replay its
                 # decisions (same qubits, other angles), on host threads (the C calls

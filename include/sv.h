@@ -287,6 +287,8 @@ typedef struct {
     size_t l2_bytes;         /* chunk budget in bytes (0: 64 MiB) */
     uint32_t no_graph;       /* 1: launch directly instead of through the CUDA graph */
     uint32_t timing;         /* 1: time the passes with CUDA events (synchronises) */
+    uint32_t no_tensor_cores; /* 1: complex64 width-4/5 gates on the CUDA cores too (default:
+                                 on the tensor cores when n >= 12) */
 } sv_batch_opts;
 
 typedef struct {
@@ -324,8 +326,8 @@ sv_status sv_batch_expect(sv_batch *b, const uint64_t *xmask, const uint64_t *zm
                           const double *coef, size_t nterms, double *out);
 sv_status sv_batch_sync(sv_batch *b);
 /* Autotuner: fuse `gates` (one representative circuit of the family) at every width
- * kmin..kmax, time the batched apply on this batch for three chunk budgets (32, 64,
- * 96 MiB), and return the fastest; results are cached per batch shape and target
+ * kmin..kmax, time the batched apply on this batch for three chunk budgets (64 MiB,
+ * 512 MiB, the whole batch), and return the fastest; results are cached per batch shape and target
  * sequence (the measure-once-and-cache idea of Algorithm 1, applied to the fusion width
  * and the chunking).  Overwrites the batch's states with |0...0>.  Synchronises. */
 sv_status sv_batch_tune(sv_batch *b, const sv_gate *gates, size_t ngates, uint32_t kmin, uint32_t kmax,

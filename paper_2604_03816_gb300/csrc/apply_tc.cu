@@ -63,7 +63,9 @@ namespace svk {
 // segments of launches whose targets are all high (2 KiB instead of 1 KiB at k = 5), at
 // the price of one more A slice in TMEM (A2 2^-9 replaces the B2 2^-9 copy, to fit two
 // 64 KiB stages in shared memory).
-template <int K, int SUB = 1>
+// BT: a batched launch over many states with their own matrices (see apply_tc): two B
+// sets (the current state's and the next one's) and two raw stages.
+template <int K, int SUB = 1, bool BT = false>
 struct TcShape {
     static constexpr uint32_t D = 1u << K;            // amplitudes per group
     static constexpr uint32_t KD = 2u * D;            // real K = N
@@ -73,7 +75,7 @@ struct TcShape {
     static constexpr uint32_t B_BYTES = KD * KD * 2u;     // one FP16 slice of B
     static constexpr uint32_t NB = SUB == 2 ? 3u : 4u;    // B1, B2, B3 2^-9 [, B2 2^-9]
     static constexpr uint32_t SBO = (KD / 8u) * 128u;     // 8-row group stride of B
-    static constexpr uint32_t NS = SUB == 2 ? 2u : (K == 5 ? 3u : 8u);   // raw stages
+    static constexpr uint32_t NS = (SUB == 2 || BT) ? 2u : (K == 5 ? 3u : 8u);   // raw stages
     static constexpr uint32_t NOUT = SUB == 2 ? 1u : 2u;  // output staging tiles
     static constexpr uint32_t ACC = 2u * KD;              // TMEM columns of one D set (D0, D12)
     static constexpr uint32_t A_COLS = KD / 2u;           // TMEM columns of one A slice
@@ -82,7 +84,9 @@ struct TcShape {
     static constexpr uint32_t A_COL0 = 2u * ACC;          // first column of the A buffers
     static constexpr uint32_t TMEM_COLS = K == 5 ? 512u : 256u;
     static_assert(A_COL0 + 2u * A_SET <= TMEM_COLS, "TMEM layout");
-    static constexpr uint32_t OFF_RAW = NB * B_BYTES;
+    static constexpr uint32_t NBSET = BT ? 2u : 1u;       // B sets
+    static constexpr uint32_t B_SET = NB * B_BYTES;
+    static constexpr uint32_t OFF_RAW = NBSET * B_SET;
     static constexpr uint32_t OFF_OUT = OFF_RAW + NS * TILE_BYTES;
     static constexpr uint32_t SMEM = OFF_OUT + NOUT * TILE_BYTES;
     static constexpr uint32_t THREADS = 576;              // 18 warps
@@ -104,6 +108,13 @@ struct TcArgs {
     // bank-conflict avoidance: the xt lowest targets sit at tile bits below 4; lane l
     // takes group members in the order c ^ x(l), x(l) = (l >> xs) & (2^xt - 1)
     uint32_t xs, xt;
+    // batched launches: ntiles = states x tiles_per_state, state i at amplitude offset
+    // i 2^n; state i's matrix is utab + i 2 4^kin (FP32 complex, row-major), of width kin
+    // = K, or K - 1 widened by an identity qubit at local bit jw (jw = -1: not widened)
+    const float *utab;
+    unsigned long long tiles_per_state;
+    uint32_t n, kin;
+    int jw;
 };
 
 // v[c] <- v[c ^ x] for the low xt bits of x: one conditional-swap stage per bit.
@@ -149,13 +160,72 @@ __device__ __forceinline__ void slice3(float2 v, float scale, uint32_t &w1, uint
     w3 = pack_half2(r3 * (1.f / 512.f), i3 * (1.f / 512.f));
 }
 
+// Batched launches build B in shared memory from a state's FP32 matrix (width kin, or
+// K - 1 widened by an identity qubit at local bit jw): entry (r, c) of the K-qubit U.
+__device__ __forceinline__ float u_entry(const float *U, uint32_t kin, int jw, uint32_t r, uint32_t c,
+                                         uint32_t part) {
+    if (jw >= 0) {
+        if (((r ^ c) >> jw) & 1u) return 0.f;
+        const uint32_t lo = (1u << jw) - 1u;
+        r = (r & lo) | ((r >> (jw + 1)) << jw);
+        c = (c & lo) | ((c >> (jw + 1)) << jw);
+    }
+    return U[2u * ((r << kin) + c) + part];
+}
+
+// Largest |entry| of a state's stored matrix over the entries i0, i0 + stride, ...
+__device__ __forceinline__ float u_absmax_part(const float *U, uint32_t kin, uint32_t i0, uint32_t stride) {
+    float m = 0.f;
+    for (uint32_t i = i0; i < (2u << (2u * kin)); i += stride) m = fmaxf(m, fabsf(U[i]));
+    return m;
+}
+
+// B = the four FP16 slices (B1, B2, B3 2^-9, B2 2^-9) of R x sb, R the real embedding of
+// the state's U and sb = 2^(8 - eb) with max |R| < 2^eb, so |R sb| < 256 and the three
+// 9-bit slices of the FP32 value are exact; entries i0, i0 + stride, ...
+template <int K>
+__device__ void build_b(unsigned char *sB, const float *U, uint32_t kin, int jw, float sb, uint32_t i0,
+                        uint32_t stride) {
+    using S = TcShape<K, 1, true>;
+    constexpr uint32_t KD = S::KD;
+    for (uint32_t e = i0; e < KD * KD; e += stride) {
+        const uint32_t n = e / KD, kk = e % KD, r = n >> 1, c = kk >> 1;
+        float v;
+        if ((n & 1u) == (kk & 1u)) v = u_entry(U, kin, jw, r, c, 0);
+        else v = (n & 1u) ? u_entry(U, kin, jw, r, c, 1) : -u_entry(U, kin, jw, r, c, 1);
+        const float x = v * sb;
+        const float b1 = rintf(x);
+        const float x2 = (x - b1) * 512.f;
+        const float b2 = rintf(x2);
+        const float b3 = rintf((x2 - b2) * 512.f);
+        const uint32_t off = kmajor_off16(n, kk, S::SBO);
+        *reinterpret_cast<__half *>(sB + 0 * S::B_BYTES + off) = __float2half_rn(b1);
+        *reinterpret_cast<__half *>(sB + 1 * S::B_BYTES + off) = __float2half_rn(b2);
+        *reinterpret_cast<__half *>(sB + 2 * S::B_BYTES + off) = __float2half_rn(b3 * (1.f / 512.f));
+        *reinterpret_cast<__half *>(sB + 3 * S::B_BYTES + off) = __float2half_rn(b2 * (1.f / 512.f));
+    }
+}
+
+// sb = 2^(8 - eb) and 1 / sb for a matrix whose largest |entry| is m < 2^eb.
+__device__ __forceinline__ void b_grid(float m, float &sb, float &inv) {
+    int eb = 0;
+    frexpf(m, &eb);
+    eb = max(eb, -100);
+    sb = ldexpf(1.f, 8 - eb);
+    inv = ldexpf(1.f, eb - 8);
+}
+
 // XP: the launch has targets among tile bits 0..3 and takes members in the lane's XOR
 // order; otherwise every lane takes them in member order (no permutation code at all).
 // The pipelines count tiles (j: raw stage, output staging) and MMA subtiles (js = j SUB +
 // sub: A and D buffers, row scales).
-template <int K, bool XP, int SUB>
+// BT: one launch over a batch of states, each with its own matrix: a CTA takes a
+// contiguous range of tiles (so it meets few states), B is double-buffered and rebuilt by
+// the producer warp from the next state's matrix when its first tile comes up (b_full:
+// built; b_empty: the MMAs of the state that last used the set have completed).
+template <int K, bool XP, int SUB, bool BT = false>
 __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
-    using S = TcShape<K, SUB>;
+    using S = TcShape<K, SUB, BT>;
     constexpr uint32_t KD = S::KD, NS = S::NS, NOUT = S::NOUT, HALF = S::HALF;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
@@ -165,6 +235,9 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
     __shared__ float max_part[2][128];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    __shared__ __align__(8) unsigned long long b_full[2], b_empty[2];   // batched launches
+    __shared__ float b_scale[2];
+    __shared__ float red[32];
     // B slices, the raw stages and the output staging tiles; B operand reads stay inside
     // the CTA's shared memory whatever the descriptor strides.
     unsigned char *sB = smem;
@@ -191,25 +264,65 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
             mbar_init(smem_u32(&d_empty[b]), 1);
         }
         for (int q = 0; q < 4; ++q) mbar_init(smem_u32(&scale_full[q]), 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(smem_u32(&b_full[q]), 1);
+            mbar_init(smem_u32(&b_empty[q]), 1);
+        }
         abort_flag = 0;
         fence_mbar_init();
     }
-    for (uint32_t e = tid; e < KD * KD; e += blockDim.x) {
-        const uint32_t n = e / KD, kk = e % KD, off = kmajor_off16(n, kk, S::SBO);
-        *reinterpret_cast<__half *>(sB + 0 * S::B_BYTES + off) = __int2half_rn(a.b[0][e]);
-        *reinterpret_cast<__half *>(sB + 1 * S::B_BYTES + off) = __int2half_rn(a.b[1][e]);
-        // exact: integers below 2^9 times 2^-9
-        *reinterpret_cast<__half *>(sB + 2 * S::B_BYTES + off) = __float2half_rn(a.b[2][e] * (1.f / 512.f));
-        if constexpr (SUB == 1)
-            *reinterpret_cast<__half *>(sB + 3 * S::B_BYTES + off) = __float2half_rn(a.b[1][e] * (1.f / 512.f));
+    // tiles of this CTA: strided over the grid, or (batched) a contiguous range
+    unsigned long long first = blockIdx.x, step = gridDim.x, tend = a.ntiles;
+    if constexpr (BT) {
+        const unsigned long long per = (a.ntiles + gridDim.x - 1) / gridDim.x;
+        first = min(a.ntiles, (unsigned long long)blockIdx.x * per);
+        tend = min(a.ntiles, first + per);
+        step = 1;
+    }
+    if constexpr (BT) {
+        // B set 0 from the matrix of the range's first state, built by every thread
+        const unsigned long long st0 = first < tend ? first / a.tiles_per_state : 0;
+        const float *U0 = a.utab + st0 * (2ull << (2u * a.kin));
+        float m = u_absmax_part(U0, a.kin, tid, blockDim.x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) red[warp] = m;
+        __syncthreads();
+        m = 0.f;
+        for (uint32_t w = 0; w < S::THREADS / 32u; ++w) m = fmaxf(m, red[w]);
+        float sb, inv;
+        b_grid(m, sb, inv);
+        build_b<K>(sB, U0, a.kin, a.jw, sb, tid, blockDim.x);
+        if (tid == 0) b_scale[0] = inv;
+    } else {
+        for (uint32_t e = tid; e < KD * KD; e += blockDim.x) {
+            const uint32_t n = e / KD, kk = e % KD, off = kmajor_off16(n, kk, S::SBO);
+            *reinterpret_cast<__half *>(sB + 0 * S::B_BYTES + off) = __int2half_rn(a.b[0][e]);
+            *reinterpret_cast<__half *>(sB + 1 * S::B_BYTES + off) = __int2half_rn(a.b[1][e]);
+            // exact: integers below 2^9 times 2^-9
+            *reinterpret_cast<__half *>(sB + 2 * S::B_BYTES + off) = __float2half_rn(a.b[2][e] * (1.f / 512.f));
+            if constexpr (SUB == 1)
+                *reinterpret_cast<__half *>(sB + 3 * S::B_BYTES + off) = __float2half_rn(a.b[1][e] * (1.f / 512.f));
+        }
     }
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if constexpr (BT) {
+        if (tid == 0) mbar_arrive(smem_u32(&b_full[0]));   // set 0: its first use
+    }
     const uint32_t tmem = tmem_slot;
     volatile int *abort = &abort_flag;
-    const unsigned long long first = blockIdx.x, step = gridDim.x;
+    // amplitude offset of tile t (batched: the state's offset plus the tile's base)
+    auto tile_base = [&](const SegLanes &sl, unsigned long long t) -> unsigned long long {
+        if constexpr (BT) {
+            const unsigned long long st = t / a.tiles_per_state;
+            return (st << a.n) + sl.base(t - st * a.tiles_per_state);
+        } else {
+            return sl.base(t);
+        }
+    };
 
     auto group_base = [&](uint32_t row) {
         uint32_t g = row;
@@ -236,7 +349,34 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         SegLanes sl;
         sl.init(a.L, a.h, a.hi, lane);
         uint32_t j = 0;
-        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+        unsigned long long cur = ~0ull;
+        uint32_t nsw = 0;                         // state changes so far (B set = nsw & 1)
+        for (unsigned long long t = first; t < tend; t += step, ++j) {
+            if constexpr (BT) {
+                const unsigned long long st = t / a.tiles_per_state;
+                if (cur == ~0ull) {
+                    cur = st;                     // set 0 was built at the start
+                } else if (st != cur) {
+                    cur = st;
+                    ++nsw;
+                    const uint32_t set = nsw & 1u, use = nsw >> 1;
+                    bool okb = true;
+                    if (use >= 1 && lane == 0)
+                        okb = mbar_wait_or_abort(smem_u32(&b_empty[set]), (use - 1u) & 1u, abort);
+                    if (!__shfl_sync(0xffffffffu, (int)okb, 0)) break;
+                    const float *U = a.utab + st * (2ull << (2u * a.kin));
+                    float m = u_absmax_part(U, a.kin, lane, 32);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                    float sb, inv;
+                    b_grid(m, sb, inv);
+                    build_b<K>(sB + set * S::B_SET, U, a.kin, a.jw, sb, lane, 32);
+                    if (lane == 0) b_scale[set] = inv;
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&b_full[set]));
+                }
+            }
             const uint32_t s = j % NS, u = j / NS;
             bool ok = true;
             if (lane == 0) ok = mbar_wait_or_abort(smem_u32(&empty[s]), (u & 1u) ^ 1u, abort);
@@ -246,7 +386,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
             __syncwarp();
             if (lane < nseg) {
                 float2 *dst = reinterpret_cast<float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
-                bulk_g2s(smem_u32(dst + (size_t)lane * seg_amps), psi + sl.base(t) + sl.my_off,
+                bulk_g2s(smem_u32(dst + (size_t)lane * seg_amps), psi + tile_base(sl, t) + sl.my_off,
                          seg_bytes, bar);
             }
         }
@@ -254,10 +394,25 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(S::ROWS, KD);
-            const uint32_t B0 = smem_u32(sB);
-            const unsigned long long nsub = a.ntiles > first
-                                                ? ((a.ntiles - first + step - 1) / step) * SUB : 0;
+            uint32_t B0 = smem_u32(sB);
+            const unsigned long long nsub = tend > first ? ((tend - first + step - 1) / step) * SUB : 0;
+            unsigned long long cur = ~0ull;
+            uint32_t nsw = 0;
             for (unsigned long long js = 0; js < nsub; ++js) {
+                if constexpr (BT) {
+                    const unsigned long long st = (first + (js / SUB) * step) / a.tiles_per_state;
+                    if (st != cur) {
+                        if (cur != ~0ull) {
+                            mma_commit(smem_u32(&b_empty[nsw & 1u]));   // the old state's MMAs
+                            ++nsw;
+                        }
+                        cur = st;
+                        const uint32_t set = nsw & 1u, use = nsw >> 1;
+                        if (!mbar_wait_or_abort(smem_u32(&b_full[set]), use & 1u, abort)) break;
+                        tc_fence_after();
+                        B0 = smem_u32(sB) + set * S::B_SET;
+                    }
+                }
                 const uint32_t b = (uint32_t)js & 1u, u = (uint32_t)(js >> 1);
                 if (!mbar_wait_or_abort(smem_u32(&a_full[b]), u & 1u, abort)) break;
                 if (!mbar_wait_or_abort(smem_u32(&d_empty[b]), (u & 1u) ^ 1u, abort)) break;
@@ -300,7 +455,14 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
             if ((xl >> q) & 1u) cx |= tbit[q];
         uint32_t j = 0;
         bool stop = false;
-        for (unsigned long long t = first; t < a.ntiles && !stop; t += step, ++j) {
+        unsigned long long cur = ~0ull;
+        uint32_t nsw = 0;
+        for (unsigned long long t = first; t < tend && !stop; t += step, ++j) {
+            if constexpr (BT) {
+                const unsigned long long st = t / a.tiles_per_state;
+                if (cur != ~0ull && st != cur) ++nsw;
+                cur = st;
+            }
             const uint32_t s = j % NS;
             const bool okf = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
             const float2 *rs = reinterpret_cast<const float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
@@ -333,7 +495,8 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
                 // slot js & 3 was last read by the epilogue of subtile js - 4, which finished
                 // before the MMAs of subtile js - 2 were issued, whose completion released
                 // a_empty[ab]
-                if (part == 0) row_scale[js & 3u][row] = ldexpf(a.b_inv_scale, ex - 8);
+                // batched: the state's B scale, written by the producer before this tile's load
+                if (part == 0) row_scale[js & 3u][row] = ldexpf(BT ? b_scale[nsw & 1u] : a.b_inv_scale, ex - 8);
                 if constexpr (XP) xor_unpermute(v, xl, a.xt);   // back in member order (x < HALF)
                 // three 9-bit integer slices (and A2 2^-9 when SUB = 2), one FP16 pair
                 // (re, im) per 32-bit TMEM column, stored eight members at a time
@@ -380,7 +543,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         sl.init(a.L, a.h, a.hi, lane);
         uint32_t j = 0;
         bool stop = false;
-        for (unsigned long long t = first; t < a.ntiles && !stop; t += step, ++j) {
+        for (unsigned long long t = first; t < tend && !stop; t += step, ++j) {
             const uint32_t ob = j % NOUT;
             float2 *out = reinterpret_cast<float2 *>(smem + S::OFF_OUT + ob * S::TILE_BYTES);
 #pragma unroll
@@ -424,7 +587,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
             if (stop) break;
             if (et < 32) {
                 if (lane < nseg)
-                    bulk_s2g(psi + sl.base(t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
+                    bulk_s2g(psi + tile_base(sl, t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
                              seg_bytes);
                 bulk_commit();
             }
@@ -510,6 +673,78 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     } else {
         apply_tc<K, false, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     }
+    SV_CUDA(cudaGetLastError());
+    return SV_OK;
+}
+
+// Batched launches (sv_batch_apply): complex64 gates of width 4 or 5 on states of at least
+// 12 qubits run as width-5 gates (a width-4 gate widened by an identity qubit, chosen as
+// in widen_gate) with one MMA subtile per stage; each state's B is built on the device
+// from the batch's FP32 matrix table.
+template <bool XP>
+static cudaError_t tc_batch_setup() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(apply_tc<5, XP, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)TcShape<5, 1, true>::SMEM);
+    });
+    return err;
+}
+
+cudaError_t tc_batch_prepare() {
+    cudaError_t e = tc_batch_setup<false>();
+    return e == cudaSuccess ? tc_batch_setup<true>() : e;
+}
+
+sv_status launch_tc_batch(const sv_batch_launch &L) {
+    using S = TcShape<5, 1, true>;
+    const cudaError_t e0 = tc_batch_prepare();
+    if (e0 != cudaSuccess)
+        return svi::set_error(SV_ERR_CUDA, std::string("batched tensor-core kernel setup: ") + cudaGetErrorString(e0));
+    uint32_t t5[5];
+    int jw = -1;
+    if (L.k == 5) {
+        for (int j = 0; j < 5; ++j) t5[j] = L.t[j];
+    } else {
+        // the identity qubit: the smallest non-target at or above bit 5, else below it
+        bool used[64] = {false};
+        for (uint32_t j = 0; j < 4; ++j) used[L.t[j]] = true;
+        uint32_t q = 64;
+        for (uint32_t c = 5; c < L.n && q == 64; ++c)
+            if (!used[c]) q = c;
+        for (uint32_t c = 0; c < L.n && q == 64; ++c)
+            if (!used[c]) q = c;
+        uint32_t m = 0;
+        for (uint32_t j = 0; j < 4; ++j) {
+            if (q < L.t[j] && jw < 0) { jw = (int)m; t5[m++] = q; }
+            t5[m++] = L.t[j];
+        }
+        if (jw < 0) { jw = (int)m; t5[m++] = q; }
+    }
+    const Plan p = make_plan(L.n, 5, t5, S::TB);
+    uint32_t tl = 0;
+    while (tl < 5u && p.lp[tl] < 4u) ++tl;
+    TcArgs<5> a;
+    std::memset(a.b, 0, sizeof(a.b));
+    a.b_inv_scale = 1.f;
+    a.psi = L.psi;
+    a.err = L.err;
+    a.ntiles = p.ntiles * L.states;
+    a.L = p.L;
+    a.h = p.h;
+    for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
+    for (int j = 0; j < 5; ++j) a.lp[j] = p.lp[j];
+    a.xs = 4u - tl;
+    a.xt = std::min(tl, 4u);
+    a.utab = static_cast<const float *>(L.utab);
+    a.tiles_per_state = p.ntiles;
+    a.n = L.n;
+    a.kin = L.k;
+    a.jw = jw;
+    const unsigned grid = (unsigned)std::min<unsigned long long>(a.ntiles, (unsigned long long)L.num_sms);
+    if (a.xt >= 1) apply_tc<5, true, 1, true><<<grid, S::THREADS, S::SMEM, L.stream>>>(a);
+    else apply_tc<5, false, 1, true><<<grid, S::THREADS, S::SMEM, L.stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }

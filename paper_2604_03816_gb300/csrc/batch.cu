@@ -7,7 +7,8 @@
 // Execution: the states are processed in chunks small enough to stay resident in L2;
 // for each chunk every fused gate is one launch of a persistent tile kernel that strides
 // over all tiles of the chunk's states (the tile geometry is the one of the single-state
-// kernels: TMA 1-D bulk staging of 2^h segments, one HBM/L2 read + write per gate).  The
+// kernels: TMA 1-D bulk staging of 2^h segments, one HBM/L2 read + write per gate;
+// complex64 gates of width 4 and 5 run on the tensor-core kernel of apply_tc.cu).  The
 // whole launch sequence is captured once into a CUDA graph and replayed while the batch
 // object, the chunk size and the fused structure stay the same; only the matrix table is
 // refreshed (an H2D copy before the replay).
@@ -20,6 +21,8 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <system_error>
+#include <thread>
 
 #include "plan.h"
 #include "ptx.cuh"
@@ -224,8 +227,28 @@ __global__ void batch_expect_kernel(const __grid_constant__ BatchExpectArgs a, c
     const C *psi = reinterpret_cast<const C *>(psi_) + ((unsigned long long)blockIdx.y << a.n);
     double acc = 0.0;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.npairs;
-         i += stride) {
+    // Z-only terms: runs of eight consecutive amplitudes per thread, the term weights and
+    // the run's sum in the state's precision (FP32 for complex64: GB300's FP64 pipe is
+    // narrow), one FP64 add per run
+    __shared__ R cw[BEXP_TERMS];
+    if (threadIdx.x < BEXP_TERMS) cw[threadIdx.x] = (R)a.ccr[threadIdx.x];
+    __syncthreads();
+    const unsigned long long nrun = a.x == 0 ? a.npairs / 8 : 0;
+    for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrun;
+         r += stride) {
+        R run = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const unsigned long long i = r * 8 + q;
+            const C v = psi[i];
+            R w = 0;
+            for (int t = 0; t < a.nterms; ++t) w += (__popcll(i & a.z[t]) & 1) ? -cw[t] : cw[t];
+            run += w * bprob(v.x, v.y);
+        }
+        acc += (double)run;
+    }
+    for (unsigned long long i = nrun * 8 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+         i < a.npairs; i += stride) {
         if (a.x == 0) {
             const C v = psi[i];
             double w = 0.0;
@@ -308,6 +331,7 @@ namespace svi {
 static size_t elem_bytes_b(sv_dtype d) { return d == SV_C64 ? 8 : 16; }
 
 static sv_status batch_launch(const sv_batch_launch &L) {
+    if (L.tc) return svk::launch_tc_batch(L);
     if (L.dtype == SV_C64) {
         switch (L.k) {
             case 1: return svk::BatchKernel<float, 1>::launch(L);
@@ -493,25 +517,51 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
         }
     }
     if (b->staged_pending) SV_CUDA(cudaEventSynchronize(b->staged));   // staging buffer is free
-    for (size_t g = 0; g < G; ++g) {
-        const size_t d2 = (size_t)1 << (2 * c0->gates[g].k);
-        char *dst = static_cast<char *>(b->utab_host) + goff[g];
-        for (uint32_t i = 0; i < b->count; ++i) {
-            const std::vector<cplx> &u = circuits[i]->gates[g].u;
-            if (b->dtype == SV_C64) {
-                float *f = reinterpret_cast<float *>(dst) + (size_t)i * 2 * d2;
-                for (size_t e = 0; e < d2; ++e) {
-                    f[2 * e] = (float)u[e].real();
-                    f[2 * e + 1] = (float)u[e].imag();
-                }
-            } else {
-                double *f = reinterpret_cast<double *>(dst) + (size_t)i * 2 * d2;
-                for (size_t e = 0; e < d2; ++e) {
-                    f[2 * e] = u[e].real();
-                    f[2 * e + 1] = u[e].imag();
+    // the table [gate][state][2 4^k] in the state's precision, states split over host threads
+    auto fill = [&](uint32_t i0, uint32_t i1) {
+        for (size_t g = 0; g < G; ++g) {
+            const size_t d2 = (size_t)1 << (2 * c0->gates[g].k);
+            char *dst = static_cast<char *>(b->utab_host) + goff[g];
+            for (uint32_t i = i0; i < i1; ++i) {
+                const std::vector<cplx> &u = circuits[i]->gates[g].u;
+                if (b->dtype == SV_C64) {
+                    float *f = reinterpret_cast<float *>(dst) + (size_t)i * 2 * d2;
+                    for (size_t e = 0; e < d2; ++e) {
+                        f[2 * e] = (float)u[e].real();
+                        f[2 * e + 1] = (float)u[e].imag();
+                    }
+                } else {
+                    double *f = reinterpret_cast<double *>(dst) + (size_t)i * 2 * d2;
+                    for (size_t e = 0; e < d2; ++e) {
+                        f[2 * e] = u[e].real();
+                        f[2 * e + 1] = u[e].imag();
+                    }
                 }
             }
         }
+    };
+    {
+        const size_t work = tab / 4;                      // entries to convert, roughly
+        const uint32_t hw = std::max(1u, std::thread::hardware_concurrency());
+        const uint32_t nt = (uint32_t)std::min<size_t>({(size_t)std::min(hw, 16u), (size_t)b->count,
+                                                        std::max<size_t>(1, work >> 18)});
+        std::vector<std::thread> th;
+        const uint32_t per = (b->count + nt - 1) / nt;
+        try {
+            for (uint32_t w = 1; w < nt; ++w) {
+                const uint32_t i0 = std::min(b->count, w * per), i1 = std::min(b->count, i0 + per);
+                if (i0 < i1) th.emplace_back(fill, i0, i1);
+            }
+        } catch (const std::system_error &) {
+            // no more threads: the calling thread fills the rest below
+        }
+        const uint32_t done_by_threads = (uint32_t)th.size();
+        fill(0, std::min(b->count, per));
+        for (uint32_t w = done_by_threads + 1; w < nt; ++w) {
+            const uint32_t i0 = std::min(b->count, w * per), i1 = std::min(b->count, i0 + per);
+            if (i0 < i1) fill(i0, i1);
+        }
+        for (std::thread &t : th) t.join();
     }
     SV_CUDA(cudaMemcpyAsync(b->utab, b->utab_host, tab, cudaMemcpyHostToDevice, b->stream));
     SV_CUDA(cudaEventRecord(b->staged, b->stream));
@@ -524,9 +574,13 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
     chunk = std::min(chunk, b->count);
     const bool use_graph = !(opts && opts->no_graph);
     const bool timing = opts && opts->timing;
+    // complex64 gates of width 4 and 5 on the tensor cores (states of at least 12 qubits)
+    const bool tc_ok = b->dtype == SV_C64 && b->n >= 12 && !(opts && opts->no_tensor_cores);
+    auto use_tc = [&](const Gate &g) { return tc_ok && (g.k == 4 || g.k == 5); };
 
     std::string key = std::to_string(b->n) + "/" + std::to_string(b->count) + "/" +
-                      std::to_string(b->dtype) + "/" + std::to_string(chunk) + "/";
+                      std::to_string(b->dtype) + "/" + std::to_string(chunk) + "/" +
+                      (tc_ok ? "tc/" : "cc/");
     for (const Gate &g : c0->gates)
         for (uint32_t j = 0; j < g.k; ++j) key += std::to_string(g.t[j]) + (j + 1 < g.k ? "," : ";");
 
@@ -547,6 +601,7 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
                 L.err = b->err;
                 L.stream = stream;
                 L.num_sms = b->num_sms;
+                L.tc = use_tc(gg);
                 sv_status st = batch_launch(L);
                 if (st != SV_OK) return st;
             }
@@ -566,7 +621,7 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
         if (st != SV_OK) return st;
     } else {
         if (!b->graph || b->graph_key != key) {
-            for (const Gate &g : c0->gates) SV_CUDA(batch_prepare(b->dtype, g.k));
+            for (const Gate &g : c0->gates) SV_CUDA(use_tc(g) ? svk::tc_batch_prepare() : batch_prepare(b->dtype, g.k));
             if (b->graph) {
                 cudaGraphExecDestroy(b->graph);
                 b->graph = nullptr;
@@ -685,7 +740,10 @@ sv_status sv_batch_tune(sv_batch *b, const sv_gate *gates, size_t ngates, uint32
     sv_tune_result r;
     std::memset(&r, 0, sizeof(r));
     double best = 1e300;
-    const size_t l2s[3] = {size_t(32) << 20, size_t(64) << 20, size_t(96) << 20};
+    // chunk budgets: L2-resident chunks suit the CUDA-core passes; the tensor-core passes
+    // (a fixed cost of about 20 us per launch) prefer few large launches
+    const size_t sbytes = (b->dtype == SV_C64 ? size_t(8) : size_t(16)) << b->n;
+    const size_t l2s[3] = {size_t(64) << 20, size_t(512) << 20, sbytes * b->count};
     for (uint32_t k = kmin; k <= kmax; ++k) {
         sv_circuit *c = nullptr;
         sv_status st = sv_fuse(gates, ngates, b->n, k, &c);

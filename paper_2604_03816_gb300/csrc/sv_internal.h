@@ -113,7 +113,13 @@ struct sv_batch_launch {
     int *err = nullptr;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
+    bool tc = false;            // complex64 width 4/5 on the tensor cores (apply_tc.cu)
 };
+
+namespace svk {
+cudaError_t tc_batch_prepare();
+sv_status launch_tc_batch(const sv_batch_launch &L);
+}  // namespace svk
 
 namespace svi {
 // ---- kernels (apply_kernels.cu / reduce_kernels.cu); all enqueue on s->stream ----

@@ -72,7 +72,8 @@ class sv_apply_report(ctypes.Structure):
 
 class sv_batch_opts(ctypes.Structure):
     _fields_ = [("chunk_states", ctypes.c_uint32), ("l2_bytes", ctypes.c_size_t),
-                ("no_graph", ctypes.c_uint32), ("timing", ctypes.c_uint32)]
+                ("no_graph", ctypes.c_uint32), ("timing", ctypes.c_uint32),
+                ("no_tensor_cores", ctypes.c_uint32)]
 
 
 class sv_batch_report(ctypes.Structure):
@@ -530,10 +531,12 @@ def sv_batch_get_state(b: Batch, i: int) -> np.ndarray:
 
 
 def sv_batch_apply(b: Batch, circuits: Sequence[Circuit], chunk_states: int = 0,
-                   l2_bytes: int = 0, no_graph: bool = False, timing: bool = False) -> dict:
+                   l2_bytes: int = 0, no_graph: bool = False, timing: bool = False,
+                   no_tensor_cores: bool = False) -> dict:
     arr = (_vp * len(circuits))(*[c.handle for c in circuits])
     assert len(circuits) == b.count
-    opts = sv_batch_opts(chunk_states, l2_bytes, int(bool(no_graph)), int(bool(timing)))
+    opts = sv_batch_opts(chunk_states, l2_bytes, int(bool(no_graph)), int(bool(timing)),
+                         int(bool(no_tensor_cores)))
     rep = sv_batch_report()
     _check(_lib.sv_batch_apply(b.handle, arr, ctypes.byref(opts), ctypes.byref(rep)))
     return {"passes": rep.passes, "launches": rep.launches, "bytes": rep.bytes,

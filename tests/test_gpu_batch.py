@@ -90,3 +90,32 @@ def test_batch_tune_picks_and_caches(gpu):
     # the states were reset to |0...0>
     assert sv.sv_batch_get_state(b, 0)[0] == 1
     b.free()
+
+
+@pytest.mark.parametrize("n", [12, 14])
+@pytest.mark.parametrize("k", [4, 5])
+def test_batch_tensor_cores_match_oracle(gpu, n, k):
+    """complex64 width-4/5 gates of a batch run on the tensor cores (width 4 widened by an
+    identity qubit in the kernel, B built per state on the device): each state against
+    the oracle, and against the CUDA-core batched path.  Small states and a chunk size
+    that is not a multiple of anything make CTAs' tile ranges cross state boundaries (a
+    12-qubit state is one tile)."""
+    import torch
+    sv = gpu
+    count = 23
+    specs = [W.hea(n, 3, seed=300 + i) for i in range(count)]
+    circs = [sv.sv_fuse(sv.gates_from_specs(sp), n, k) for sp in specs]
+    assert any(len(sv.sv_circuit_gate(circs[0], g)[0]) == k for g in range(len(circs[0])))
+    outs = {}
+    for no_tc in (False, True):
+        b = sv.sv_batch_alloc(n, 0, count, stream=torch.cuda.current_stream())
+        sv.sv_batch_apply(b, circs, chunk_states=7, no_tensor_cores=no_tc)
+        sv.sv_batch_sync(b)
+        outs[no_tc] = [sv.sv_batch_get_state(b, i).astype(np.complex128) for i in range(count)]
+        b.free()
+    for i in range(count):
+        ref = oracle.simulate(n, specs[i])
+        for no_tc in (False, True):
+            err = float(np.max(np.abs(outs[no_tc][i] - ref)))
+            assert err <= 1e-5, (i, no_tc, err)
+        assert float(np.max(np.abs(outs[False][i] - outs[True][i]))) <= 2e-6
