@@ -507,8 +507,9 @@ def run_batched(args):
     """512 hardware-efficient-ansatz circuits (widths U{16,18,20,22}, 6 layers of
     RY RZ + CNOT ladder, complex64), <sum Z_i Z_{i+1}> per circuit.  Per width: one batch,
     fusion width and chunking from the autotuner (tuned once, before timing).  One step =
-    fusion of every circuit (sv_fuse for one, sv_fuse_like for the rest) + sv_batch_apply
-    per width (CUDA-graph replay) + sv_batch_expect per width."""
+    fusion of every circuit (sv_fuse for one, sv_fuse_like for the rest; the widest
+    width's for the next step overlaps this step's GPU work) + sv_batch_apply per width
+    (CUDA-graph replay) + sv_batch_expect per width."""
     import torch
     from paper_2604_03816_gb300 import sv
     rank, world, local = dist_info()
@@ -527,22 +528,30 @@ def run_batched(args):
             batches[w] = sv.sv_batch_alloc(w, sv.SV_C64, len(groups[w]), stream=stream)
             tune[w] = sv.sv_batch_tune(batches[w], gates[w][0], 1, 5)
 
+        def fuse_width(w):
+            # Algorithm 2 once per width; the other circuits of the family replay its
+            # decisions (same qubits, other angles), on host threads (the C calls release
+            # the GIL)
+            pattern = sv.sv_fuse(arrays[w][0], w, tune[w]["best_k"])
+            return [pattern] + list(pool.map(lambda ga: sv.sv_fuse_like(pattern, ga), arrays[w][1:]))
+
+        order = sorted(widths, reverse=True)
+        fuser = cf.ThreadPoolExecutor(max_workers=1)
+        ahead = [fuser.submit(fuse_width, order[0])]
+
         def step():
             fuse_s = 0.0
             out = {}
             # widest first: its passes (most of the GPU time) overlap the host work
-            # (fusion, matrix tables) of the narrower ones
-            for w in sorted(widths, reverse=True):
+            # (fusion, matrix tables) of the narrower ones; the widest width of the next
+            # step is fused while this step's expectation values are computed
+            for w in order:
                 t0 = time.perf_counter()
-                # Algorithm 2 once per width; the other circuits of the family replay its
-                # decisions (same qubits, other angles), on host threads (the C calls
-                # release the GIL) while the GPU runs the previous width
-                pattern = sv.sv_fuse(arrays[w][0], w, tune[w]["best_k"])
-                circs = [pattern] + list(pool.map(lambda ga: sv.sv_fuse_like(pattern, ga),
-                                                  arrays[w][1:]))
+                circs = ahead[0].result() if w == order[0] else fuse_width(w)
                 fuse_s += time.perf_counter() - t0
                 sv.sv_batch_set_basis(batches[w], 0)
                 sv.sv_batch_apply(batches[w], circs, l2_bytes=tune[w]["l2_bytes"])
+            ahead[0] = fuser.submit(fuse_width, order[0])
             for w in widths:
                 xs, zs, cs = W.zz_chain(w)
                 out[w] = sv.sv_batch_expect(batches[w], xs, zs, cs)
@@ -552,14 +561,17 @@ def run_batched(args):
             step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
         fuse_total = 0.0
-        for _ in range(args.steps):
-            fs, out = step()
-            fuse_total += fs
-        e1.record(stream)
-        torch.cuda.synchronize()
+        with ClockSampler(None) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                fs, out = step()
+                fuse_total += fs
+            e1.record(stream)
+            torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        ahead[0].result()
+        fuser.shutdown(wait=True)
         # the same circuits one by one through sv_apply_circuit (unbatched), for context
         s1 = sv.sv_alloc(max(widths), sv.SV_C64, stream=stream)
         sample = [(w, gates[w][i]) for w in widths for i in range(4)]
@@ -588,7 +600,7 @@ def run_batched(args):
                                              "tune_ms": tune[w]["ms"]} for w in widths}},
            "host_fusion_s_per_step": fuse_total / args.steps,
            "unbatched_circuits_per_s": unb,
-           "speedup_vs_unbatched": value / unb}
+           "speedup_vs_unbatched": value / unb, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
 
