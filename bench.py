@@ -87,6 +87,8 @@ def parse():
     ap.add_argument("--p-depol", type=float, default=0.01, help="noise: depolarizing p")
     ap.add_argument("--noise-n", type=int, default=15, help="noise: qubits of the density matrix")
     ap.add_argument("--count", type=int, default=512, help="batched: number of circuits")
+    ap.add_argument("--batch-k", type=int, default=0,
+                    help="batched: fixed fusion width with whole-batch chunks (0: autotune)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serve: req/s list")
     ap.add_argument("--duration", type=float, default=4.0, help="serve: seconds per rate")
     ap.add_argument("--max-requests", type=int, default=40, help="serve: requests per rate")
@@ -526,7 +528,10 @@ def run_batched(args):
     with torch.cuda.stream(stream):
         for w in widths:
             batches[w] = sv.sv_batch_alloc(w, sv.SV_C64, len(groups[w]), stream=stream)
-            tune[w] = sv.sv_batch_tune(batches[w], gates[w][0], 1, 5)
+            if args.batch_k:
+                tune[w] = {"best_k": args.batch_k, "l2_bytes": (8 << w) * len(groups[w]), "ms": {}}
+            else:
+                tune[w] = sv.sv_batch_tune(batches[w], gates[w][0], 1, 5)
 
         def fuse_width(w):
             # Algorithm 2 once per width; the other circuits of the family replay its
