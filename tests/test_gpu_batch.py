@@ -119,3 +119,28 @@ def test_batch_tensor_cores_match_oracle(gpu, n, k):
             err = float(np.max(np.abs(outs[no_tc][i] - ref)))
             assert err <= 1e-5, (i, no_tc, err)
         assert float(np.max(np.abs(outs[False][i] - outs[True][i]))) <= 2e-6
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_batch_tensor_cores_rebuild_b_across_states(gpu, k):
+    """Many small states in one chunk: each CTA's tile range crosses several states, so
+    the producer rebuilds B mid-launch and reuses both B sets.  Every state against the
+    CUDA-core batched path; a sample against the oracle."""
+    import torch
+    sv = gpu
+    n, count = 13, 400            # 2 tiles per state, 800 tiles over 152 CTAs
+    rng = np.random.default_rng(77 + k)
+    specs = [W.hea(n, 2, rng=rng) for _ in range(count)]
+    circs = [sv.sv_fuse(sv.gates_from_specs(sp), n, k) for sp in specs]
+    outs = {}
+    for no_tc in (False, True):
+        b = sv.sv_batch_alloc(n, 0, count, stream=torch.cuda.current_stream())
+        sv.sv_batch_apply(b, circs, l2_bytes=1 << 40, no_tensor_cores=no_tc)
+        sv.sv_batch_sync(b)
+        outs[no_tc] = np.stack([sv.sv_batch_get_state(b, i) for i in range(count)]).astype(np.complex128)
+        b.free()
+    diff = np.max(np.abs(outs[False] - outs[True]), axis=1)
+    assert float(diff.max()) <= 2e-6, int(diff.argmax())
+    for i in list(range(0, count, 37)) + [count - 1]:
+        ref = oracle.simulate(n, specs[i])
+        assert float(np.max(np.abs(outs[False][i] - ref))) <= 1e-5, i
