@@ -336,9 +336,12 @@ sv_status sv_batch_tune(sv_batch *b, const sv_gate *gates, size_t ngates, uint32
 /* ------------------------------------------------------------------ serving */
 
 /* A continuous-batching request server on the current device.  Submitted circuits are
- * fused on host threads (Algorithm 2), then admitted in arrival order while their memory
- * (Eq. 14: 2^n s + (2^k)^2 s + workspace) fits the budget and a slot is free -- requests
- * that do not fit wait in the queue (no CPU fallback).  Each slot is a CUDA stream; the
+ * fused on host threads (Algorithm 2), then admitted -- the least estimated GPU work first
+ * (passes x state bytes at the measured pass rates), with aging (a quarter second of work
+ * per second waited) so that large requests are not starved -- while their memory
+ * (Eq. 14: 2^n s + (2^k)^2 s + workspace) fits the budget and a slot is free; requests
+ * that do not fit wait in the queue (no CPU fallback).  Each slot is a pair of CUDA
+ * streams (short requests on the high-priority one); the
  * request's state is allocated from the stream-ordered pool, set to |0...0>, every fused
  * pass is applied and the top-k outcomes are returned.  Requests in different slots
  * overlap on the GPU; each result is computed by the same kernels in the same order as

@@ -2,7 +2,9 @@
 //
 // Requests (a circuit of n qubits in one precision) arrive through sv_server_submit and
 // are fused on a small pool of host threads (Algorithm 2).  One GPU worker thread admits
-// fused requests in arrival order while the HBM they need fits the budget -- the memory
+// fused requests, cheapest estimated GPU work first with aging (a request's priority
+// grows with its wait, so large ones are not starved), while the HBM they need fits the
+// budget -- the memory
 // model of Eq. 14, M = 2^n s + (2^k)^2 s + M_ws, checked against the budget instead of
 // the paper's Eq. 15 query, and queuing instead of the paper's GPU->CPU fallback -- and
 // while a slot is free.  Each slot has its own CUDA stream and workspace; a request's
@@ -14,6 +16,7 @@
 
 #include <chrono>
 #include <condition_variable>
+#include <cstddef>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -36,11 +39,19 @@ struct Request {
     sv_circuit *circuit = nullptr;     // fused
     sv_status fuse_status = SV_OK;
     size_t cost = 0;
+    double est_s = 0;                  // estimated GPU time: passes x bytes / pass rate
     double t_submit = 0, t_admit = 0, t_done = 0;
 };
 
+// Requests estimated below this run on the slot's high-priority stream, so that their
+// kernels are scheduled ahead of long requests' as SMs free up.
+constexpr double SHORT_REQUEST_S = 0.02;
+// Seconds of estimated work that one second of waiting is worth in the admission order.
+constexpr double AGING = 0.25;
+
 struct Slot {
-    sv_state state;                    // buf re-pointed per request
+    sv_state state;                    // buf (and stream) re-pointed per request
+    cudaStream_t s_hi = nullptr, s_lo = nullptr;   // high- and low-priority streams
     cudaEvent_t done = nullptr;
     double *host_p = nullptr;          // pinned 64 doubles
     unsigned long long *host_i = nullptr;
@@ -99,6 +110,10 @@ void fuser_loop(sv_server *S) {
             // Eq. 14: state + one resident gate matrix + the workspace
             r->cost = (elem_bytes_s(r->dtype) << r->n) + (size_t(1) << (2 * kmax)) * elem_bytes_s(r->dtype) +
                       svi::WS_BYTES;
+            // GPU time: a read and a write of the state per pass at the measured pass rates
+            // (complex64 about 5.5 TB/s, complex128 about 3 TB/s) plus a launch each
+            const double rate = r->dtype == SV_C64 ? 5.5e12 : 3.0e12;
+            r->est_s = (double)c->gates.size() * (2.0 * (double)(elem_bytes_s(r->dtype) << r->n) / rate + 2.5e-5);
         }
         {
             std::lock_guard<std::mutex> lock(S->mu);
@@ -111,6 +126,7 @@ void fuser_loop(sv_server *S) {
 // Enqueue one admitted request on its slot (worker thread, no lock held).
 sv_status start_request(sv_server *S, Slot &sl, Request *r) {
     sv_state &st = sl.state;
+    st.stream = r->est_s < SHORT_REQUEST_S ? sl.s_hi : sl.s_lo;
     const size_t bytes = elem_bytes_s(r->dtype) << r->n;
     void *buf = nullptr;
     SV_CUDA(cudaMallocAsync(&buf, bytes, st.stream));
@@ -120,6 +136,7 @@ sv_status start_request(sv_server *S, Slot &sl, Request *r) {
     st.cap = bytes;
     st.owned = false;
     sv_status s = sv_set_basis(&st, 0);
+    (void)S;
     for (size_t i = 0; s == SV_OK && i < r->circuit->gates.size(); ++i)
         s = svi::launch_apply(&st, r->circuit->gates[i]);
     if (s == SV_OK) s = svi::enqueue_topk(&st, sl.host_p, sl.host_i);
@@ -184,7 +201,9 @@ void worker_loop(sv_server *S) {
             finish(S, sl, st);
             progressed = true;
         }
-        // admissions, in arrival order
+        // admissions: failed or never-fitting requests first (reported at once), then the
+        // request with the least estimated work minus AGING x its wait; if that one does
+        // not fit the free memory, nothing else is admitted until it does
         while (true) {
             Request *r = nullptr;
             Slot *slot = nullptr;
@@ -192,13 +211,28 @@ void worker_loop(sv_server *S) {
             {
                 std::lock_guard<std::mutex> lock(S->mu);
                 if (S->ready.empty()) break;
-                Request *head = S->ready.front();
-                if (head->fuse_status != SV_OK || head->cost > S->cfg.budget_bytes) {
+                const double now = S->now();
+                size_t best = S->ready.size();
+                double best_key = 0.0;
+                for (size_t i = 0; i < S->ready.size(); ++i) {
+                    Request *q = S->ready[i];
+                    if (q->fuse_status != SV_OK || q->cost > S->cfg.budget_bytes) {
+                        best = i;
+                        rejected = q;
+                        break;
+                    }
+                    const double key = q->est_s - AGING * (now - q->t_submit);
+                    if (best == S->ready.size() || key < best_key) {
+                        best = i;
+                        best_key = key;
+                    }
+                }
+                Request *head = S->ready[best];
+                if (rejected) {
                     // fusion failed or it can never fit: report it instead of queuing forever
-                    S->ready.pop_front();
-                    head->t_admit = S->now();
+                    S->ready.erase(S->ready.begin() + (std::ptrdiff_t)best);
+                    head->t_admit = now;
                     S->in_use += head->cost;
-                    rejected = head;
                 } else {
                     for (Slot &sl : S->slots)
                         if (!sl.req) {
@@ -206,10 +240,10 @@ void worker_loop(sv_server *S) {
                             break;
                         }
                     if (!slot || S->in_use + head->cost > S->cfg.budget_bytes) break;
-                    S->ready.pop_front();
+                    S->ready.erase(S->ready.begin() + (std::ptrdiff_t)best);
                     r = head;
                     S->in_use += r->cost;
-                    r->t_admit = S->now();
+                    r->t_admit = now;
                     slot->req = r;
                 }
             }
@@ -275,7 +309,11 @@ sv_status sv_server_create(const sv_server_config *cfg, sv_server **out) {
         sl.state.device = S->device;
         sl.state.num_sms = S->num_sms;
         sl.state.ws = S->ws_block + WS_BYTES * i;
-        e = cudaStreamCreateWithFlags(&sl.state.stream, cudaStreamNonBlocking);
+        int lo_prio = 0, hi_prio = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.s_hi, cudaStreamNonBlocking, hi_prio);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&sl.s_lo, cudaStreamNonBlocking, lo_prio);
+        sl.state.stream = sl.s_lo;
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&sl.host_p), 64 * sizeof(double));
         if (e == cudaSuccess)
@@ -373,10 +411,12 @@ sv_status sv_server_destroy(sv_server *S) {
         if (t.joinable()) t.join();
     if (S->worker.joinable()) S->worker.join();
     for (Slot &sl : S->slots) {
-        if (sl.state.stream) {
-            cudaStreamSynchronize(sl.state.stream);
-            cudaStreamDestroy(sl.state.stream);
-        }
+        for (cudaStream_t st : {sl.s_hi, sl.s_lo})
+            if (st) {
+                cudaStreamSynchronize(st);
+                cudaStreamDestroy(st);
+            }
+        sl.state.stream = nullptr;
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.host_p) cudaFreeHost(sl.host_p);
         if (sl.host_i) cudaFreeHost(sl.host_i);

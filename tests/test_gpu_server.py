@@ -80,3 +80,23 @@ def test_admission_respects_the_budget_and_rejects_what_never_fits(gpu):
     assert all(got[i]["status"] == 0 for i in ids)
     ref = got[ids[0]]
     assert all(np.array_equal(got[i]["idx"], ref["idx"]) for i in ids)
+
+
+def test_admission_prefers_short_requests(gpu):
+    """One slot, a long request in it: a large request and then ten small ones queue
+    behind it; the small ones (least estimated work) are admitted before the large one,
+    which still completes (aging)."""
+    sv = gpu
+    srv = sv.sv_server_create(max_slots=1, max_k=4)
+    blocker = sv.GateArray(sv.gates_from_specs(W.brickwork(26, 30, seed=1)))
+    big = sv.GateArray(sv.gates_from_specs(W.brickwork(24, 40, seed=2)))
+    small = [sv.GateArray(sv.gates_from_specs(W.brickwork(12, 6, seed=10 + i))) for i in range(10)]
+    b0 = sv.sv_server_submit(srv, 26, 1, blocker)
+    time.sleep(0.05)
+    b1 = sv.sv_server_submit(srv, 24, 1, big)
+    ids = [sv.sv_server_submit(srv, 12, 0, ga) for ga in small]
+    got = _drain(sv, srv, 12)
+    srv.destroy()
+    assert all(r["status"] == 0 for r in got.values())
+    assert got[b0]["t_admit"] < got[b1]["t_admit"]
+    assert max(got[i]["t_admit"] for i in ids) < got[b1]["t_admit"]
