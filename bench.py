@@ -42,9 +42,9 @@ FALLBACK_HBM_GBS = 6800.0
 # as null once those sources hash differently).
 KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
-            "sha256_prefix": "3cf35838b811e8b1", "n": 30,
-            "bytes_per_launch": (1.073832e9 + 1.013200e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,*,*> 72.7% of GPU time, all apply kernels "
+            "sha256_prefix": "2c8c524322c9a611", "n": 30,
+            "bytes_per_launch": (1.073810e9 + 1.014305e9) * 8,
+            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 72.7% of GPU time, all apply kernels "
                       "97.2% (profiles/fused_pass_grid30q_k5_launches.md)",
             "traffic_source": "apply_tc<5,0,2> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
