@@ -236,15 +236,23 @@ __global__ void batch_expect_kernel(const __grid_constant__ BatchExpectArgs a, c
     const unsigned long long nrun = a.x == 0 ? a.npairs / 8 : 0;
     for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrun;
          r += stride) {
+        C v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = psi[r * 8 + q];
+        // terms outside, the eight amplitudes inside: eight independent weight sums
+        R w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w[q] = 0;
+        for (int t = 0; t < a.nterms; ++t) {
+            const unsigned long long z = a.z[t];
+            const R c = cw[t];
+            const int hi = __popcll((r * 8) & z);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w[q] += ((hi + __popc((uint32_t)q & (uint32_t)z)) & 1) ? -c : c;
+        }
         R run = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const unsigned long long i = r * 8 + q;
-            const C v = psi[i];
-            R w = 0;
-            for (int t = 0; t < a.nterms; ++t) w += (__popcll(i & a.z[t]) & 1) ? -cw[t] : cw[t];
-            run += w * bprob(v.x, v.y);
-        }
+        for (int q = 0; q < 8; ++q) run += w[q] * bprob(v[q].x, v[q].y);
         acc += (double)run;
     }
     for (unsigned long long i = nrun * 8 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
