@@ -1,7 +1,10 @@
-"""Pins of the oracle's measurement sampling (oracle/sampling.py): the generator's published
-outputs, the counter structure, uniformity, chi-square agreement with the probabilities,
-a direct sequential definition on single-block states, and the block/chunk prefix against
-a flat prefix on a multi-chunk state."""
+"""Pins of the oracle's measurement sampling (oracle/sampling.py): the generator's
+published outputs and counter structure, uniformity, the fixed-point step against exact
+rationals, a brute-force definition of the drawn outcome (the interval of the exact integer
+cumulative distribution that holds the target), chi-square agreement with the
+probabilities, zero-probability outcomes never drawn, and a planted off-by-one."""
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -32,37 +35,63 @@ def test_uniforms_are_uniform():
     assert scipy_stats.kstest(u, "uniform").pvalue > 1e-3
 
 
-def _direct(p, u):
-    """Sequential definition for a single block: first k with running sum > u T."""
-    T = np.float64(0.0)
-    for v in p:
-        T = T + np.float64(v)
+def test_fixed_point_is_exact_floor():
+    rng = np.random.default_rng(8)
+    for dt in (np.float32, np.float64):
+        p = (rng.random(500) * np.exp2(rng.integers(-70, 1, 500))).astype(dt)
+        P = S.fixed(p)
+        for pk, Pk in zip(p, P):
+            q = Fraction(float(pk)) * 2 ** S.SCALE_BITS
+            assert int(Pk) == q.numerator // q.denominator
+
+
+def _brute(p, seed, nshots):
+    """Outcome i = the k with C_{k-1} <= floor(u T / 2^53) < C_k, by a linear scan with
+    Python integers."""
+    P = [int(v) for v in S.fixed(p)]
+    T = sum(P)
     out = []
-    for ui in u:
-        target = np.float64(ui) * T
-        c = np.float64(0.0)
-        k = -1
-        for j, v in enumerate(p):
-            c = c + np.float64(v)
-            if c > target:
-                k = j
+    for u in S.u53(seed, nshots):
+        target = (u * T) >> 53
+        c = 0
+        for k, v in enumerate(P):
+            if c <= target < c + v:
+                out.append(k)
                 break
-        if k < 0:
-            k = int(np.flatnonzero(p > 0)[-1])
-        out.append(k)
+            c += v
     return np.array(out, dtype=np.uint64)
 
 
-def test_single_block_matches_sequential_definition():
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_matches_brute_force_definition(dt):
     rng = np.random.default_rng(3)
-    for n in (1, 3, 6):
+    for n in (0, 1, 3, 6, 9):
         p = rng.random(1 << n)
         p[rng.integers(0, 1 << n, 1 + (1 << n) // 4)] = 0.0
         if not p.any():
             p[0] = 1.0
-        p /= p.sum()
-        got = S.sample(p, 99 + n, 500)
-        assert np.array_equal(got, _direct(p, S.uniforms(99 + n, 500)))
+        p = (p / p.sum()).astype(dt)
+        assert np.array_equal(S.sample(p, 99 + n, 400), _brute(p, 99 + n, 400))
+
+
+def test_target_interval_at_a_million_outcomes():
+    """2^20 outcomes: every drawn k satisfies C_{k-1} <= target < C_k with the exact
+    integer prefix (Python integers, independent of numpy's cumsum), and p_k > 0."""
+    rng = np.random.default_rng(5)
+    n = 20
+    p = rng.exponential(size=1 << n)
+    p[rng.integers(0, 1 << n, 1 << 16)] = 0.0
+    p = (p / p.sum()).astype(np.float32)
+    shots = S.sample(p, 31, 2000).astype(np.int64)
+    assert np.all(p[shots] > 0)
+    P = [int(v) for v in S.fixed(p)]
+    pre = [0] * (len(P) + 1)
+    for k, v in enumerate(P):
+        pre[k + 1] = pre[k] + v
+    T = pre[-1]
+    for k, u in zip(shots, S.u53(31, 2000)):
+        target = (u * T) >> 53
+        assert pre[k] <= target < pre[k + 1]
 
 
 def test_chi_square_against_probabilities():
@@ -78,27 +107,6 @@ def test_chi_square_against_probabilities():
     assert pval > 1e-4
 
 
-def test_multi_chunk_prefix_agrees_with_a_flat_prefix():
-    """2^20 outcomes = 4 chunks of 4096 blocks: the chunked prefix differs from a flat
-    sequential prefix only by rounding; every sample lies in its outcome's interval of
-    the exact (flat) cumulative distribution up to that rounding."""
-    rng = np.random.default_rng(5)
-    n = 20
-    p = rng.exponential(size=1 << n)
-    p[rng.integers(0, 1 << n, 1 << 16)] = 0.0
-    p /= p.sum()
-    B, Sb, P, T = S.block_prefix(p)
-    assert B == 64 and P.size == (1 << n) // 64
-    flat = np.concatenate([[0.0], np.cumsum(Sb)[:-1]])
-    assert np.max(np.abs(P - flat)) < 1e-12
-    shots = S.sample(p, 31, 3000)
-    assert np.all(p[shots.astype(np.int64)] > 0)
-    cdf = np.concatenate([[0.0], np.cumsum(p)])
-    u = S.uniforms(31, 3000)
-    k = shots.astype(np.int64)
-    assert np.all(cdf[k] - 1e-11 <= u * T) and np.all(u * T <= cdf[k + 1] + 1e-11)
-
-
 def test_deterministic_and_seed_dependent():
     p = np.full(256, 1.0 / 256)
     a = S.sample(p, 1, 300)
@@ -106,3 +114,14 @@ def test_deterministic_and_seed_dependent():
     assert not np.array_equal(a, S.sample(p, 2, 300))
     with pytest.raises(ValueError):
         S.sample(np.zeros(8), 1, 3)
+
+
+def test_an_off_by_one_search_is_caught(monkeypatch):
+    # Planted mistake in the oracle: side="left" picks k with C_{k-1} < target <= C_k,
+    # a neighbour (or an outcome of probability 0) whenever the target equals a prefix.
+    # Probabilities of a few units of 2^-58 make T tiny, so targets hit prefixes often.
+    p = np.array([1.0, 0.0, 1.0, 2.0]) * 2.0 ** -S.SCALE_BITS
+    real = np.searchsorted
+    monkeypatch.setattr(S.np, "searchsorted", lambda a, v, side="left": real(a, v, side="left"))
+    seeds = range(40)
+    assert any(not np.array_equal(S.sample(p, s, 64), _brute(p, s, 64)) for s in seeds)
