@@ -254,8 +254,8 @@ def run_reference(args):
 
 def run_sample(args):
     """Measurement sampling (sv_sample) from the output state of the 30-qubit grid circuit:
-    one step = one sv_sample call of --shots shots to host memory (block sums over the
-    whole state, prefix sums, the shots)."""
+    one step = one sv_sample call of --shots shots to host memory (integer block sums over
+    the whole state, prefix scans, the shots)."""
     import torch
     from paper_2604_03816_gb300 import sv
     torch.cuda.set_device(0)
@@ -283,7 +283,7 @@ def run_sample(args):
            "value": args.shots / (ms / 1000.0), "unit": "shots/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64 sums", "data": "synthetic",
+           "dtype": "u64 sums", "data": "synthetic",
            "config": {"workload": f"grid_random {args.n}q depth {args.cycles}, {args.dtype}, "
                                   f"{args.shots} shots per call to host memory",
                       "state_bytes": sbytes, "seed": W.seed_for(3, args.n),
@@ -291,8 +291,8 @@ def run_sample(args):
            "roofline": {"bound": "hbm", "achieved": sbytes / (ms / 1000.0) / 1e9, "peak": peak,
                         "unit": "GB/s", "frac": sbytes / (ms / 1000.0) / 1e9 / peak,
                         "traffic": None, "peak_kind": peak_kind,
-                        "kernel": "whole call (one read of the state for the FP64 block "
-                                  "sums, then prefix and shots)"},
+                        "kernel": "whole call (one read of the state for the integer block "
+                                  "sums, then prefix scans and shots)"},
            "cpu_baseline": None, "e2e": None, "gpu_launches": 4 * args.steps,
            "clocks": clk.summary(), "last_shots_head": [int(v) for v in shots[:4]]}
     print(json.dumps(out), flush=True)

@@ -224,16 +224,14 @@ sv_status sv_fuse_density(const sv_gate *gates, size_t ngates, uint32_t n, doubl
  * float (C64) or double (C128); host or device memory as in sv_probs. */
 sv_status sv_density_probs(sv_state *s, void *out, int out_on_device);
 /* Measurement sampling, the backend's third operation (Section 4.1; the paper prints no
- * procedure): nshots outcome indices drawn from p_k = |alpha_k|^2 / sum_j |alpha_j|^2.
- * Fixed procedure, reproducible bit for bit: p_k in the state's precision widened to
- * FP64; FP64 block sums over 64 outcomes in index order; chunk-local exclusive prefixes
- * of 4096 blocks plus the exclusive prefix of the chunk totals (index order), T = total;
- * shot i: u = (SplitMix64(seed + (i+1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53, target =
- * u * T; the largest block whose prefix is <= target and whose sum is > 0, then the first
- * outcome of the block whose running sum exceeds target - prefix (else its last outcome
- * with p > 0).  Outcomes with p = 0 are never drawn.
+ * procedure): nshots outcome indices drawn from p_k = |alpha_k|^2 / sum_j |alpha_j|^2,
+ * reproducible bit for bit from an exact integer distribution: P_k = floor(p_k 2^58) with
+ * p_k = |alpha_k|^2 in the state's precision; C_k = P_0 + ... + P_k, T = C_{N-1}; shot i:
+ * u = SplitMix64(seed + (i+1) * 0x9E3779B97F4A7C15) >> 11 (53 bits), target =
+ * floor(u T / 2^53); the outcome is the k with C_{k-1} <= target < C_k.  Outcomes with
+ * P_k = 0 are never drawn.  Valid for states of norm below 64 (the sums stay below 2^64).
  * out: nshots uint64 (host or device memory per out_on_device).  Temporary device memory:
- * 2^n / 4 bytes.  SV_ERR_STATE if the state has zero norm.  Synchronises for host output. */
+ * 2^n / 4 bytes.  SV_ERR_STATE if T = 0 (a zero state).  Synchronises for host output. */
 sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64_t *out, int out_on_device);
 /* The min(k, 2^n) most probable outcomes (1 <= k <= 64), sorted by probability
  * descending, ties to the lower index.  idx/p are host arrays of k entries.  Synchronises. */

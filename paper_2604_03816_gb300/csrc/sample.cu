@@ -1,20 +1,23 @@
 // Measurement sampling, the backend's third operation next to initialisation and gate
-// application (Section 4.1).  The paper prints no procedure; this one fixes the order of
-// every floating-point step, so the sampled indices are reproducible bit for bit:
+// application (Section 4.1).  The paper prints no procedure; this one draws from an exact
+// integer cumulative distribution, so the sampled indices are reproducible bit for bit
+// and every prefix sum may be formed in parallel:
 //
-// 1. p_k = |alpha_k|^2 in the state's precision, widened to FP64.
-// 2. Blocks of B = min(64, 2^n) outcomes: S_b = sum of the block's p_k in index order.
-// 3. Chunks of C = min(4096, #blocks) blocks: L_b = exclusive prefix of the S_b within the
-//    chunk (index order), chunk totals, O_c = exclusive prefix of the totals (index order),
-//    T = their sum; the block prefix is P_b = O_{chunk(b)} + L_b.
-// 4. Shot i: u = (SplitMix64(seed + (i + 1) * 0x9E3779B97F4A7C15) >> 11) * 2^-53 (Steele,
-//    Lea and Flood's generator as an output function of a counter), target = u * T.
-// 5. b = the largest block with P_b <= target and S_b > 0; r = target - P_b; the outcome is
-//    the block's first k whose running sum exceeds r, else its last outcome with p_k > 0.
+// 1. p_k = |alpha_k|^2 in the state's precision (FP32 for complex64, FP64 for
+//    complex128), no contraction.
+// 2. P_k = floor(p_k 2^58), from the bits of p_k (exponent and mantissa, integer shifts).
+// 3. Blocks of B = min(64, 2^n) outcomes: S_b = sum of the block's P_k (uint64, one warp
+//    per block); chunks of C = min(4096, #blocks) blocks: L_b = exclusive prefix of the
+//    S_b within the chunk (a shared-memory scan), chunk totals, O_c = their exclusive
+//    prefix and T = the total; the block prefix is P_b = O_{chunk(b)} + L_b.
+// 4. Shot i: z = SplitMix64(seed + (i + 1) * 0x9E3779B97F4A7C15) (Steele, Lea and Flood's
+//    generator as an output function of a counter), target = floor((z >> 11) T / 2^53),
+//    one 64 x 64 -> 128-bit high product.
+// 5. b = the largest block with P_b <= target (then target < P_b + S_b: S_b > 0); the
+//    outcome is the block's first k whose running sum of P exceeds target - P_b.
 //
-// Step 2 reads the state once (one thread per block, FP64 adds: about 4 ms at 30 qubits,
-// bound by this GPU's FP64 rate); steps 3-4 touch 2^n / 64 doubles; each shot reads one
-// block of the state.
+// Step 3 reads the state once (coalesced, integer work only for complex64; complex128
+// computes p_k on the FP64 pipe); each shot reads one block of the state.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +29,8 @@
 namespace svk {
 
 constexpr unsigned long long SM_GAMMA = 0x9E3779B97F4A7C15ull;
+constexpr int SCALE_BITS = 58;
+constexpr uint32_t SCAN_THREADS = 512, SCAN_ITEMS = 8;   // chunk = 4096 blocks
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -33,93 +38,152 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-// |alpha|^2 in the state's precision, no contraction, widened to FP64.
-__device__ __forceinline__ double sprob(const float2 *psi, unsigned long long k) {
-    const float2 v = psi[k];
-    return (double)__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
+// floor(p 2^58) from the IEEE bits of p >= 0.
+__device__ __forceinline__ unsigned long long fixed_of(float p) {
+    const uint32_t b = __float_as_uint(p);
+    const int e = (int)(b >> 23);
+    if (e == 0) return 0ull;                                  // below 2^-126: floor is 0
+    const unsigned long long m = (b & 0x7FFFFFu) | 0x800000u; // p = m 2^(e - 150)
+    const int sh = e - 150 + SCALE_BITS;
+    if (sh >= 0) return m << sh;
+    return sh <= -64 ? 0ull : m >> (-sh);
 }
-__device__ __forceinline__ double sprob(const double2 *psi, unsigned long long k) {
-    const double2 v = psi[k];
-    return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y));
+__device__ __forceinline__ unsigned long long fixed_of(double p) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+    const int e = (int)(b >> 52);
+    if (e == 0) return 0ull;
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);   // p = m 2^(e - 1075)
+    const int sh = e - 1075 + SCALE_BITS;
+    if (sh >= 0) return m << sh;
+    return sh <= -64 ? 0ull : m >> (-sh);
 }
 
+// P_k of amplitude k: |alpha|^2 in the state's precision, no contraction.
+__device__ __forceinline__ unsigned long long pfix(const float2 *psi, unsigned long long k) {
+    const float2 v = psi[k];
+    return fixed_of(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)));
+}
+__device__ __forceinline__ unsigned long long pfix(const double2 *psi, unsigned long long k) {
+    const double2 v = psi[k];
+    return fixed_of(__dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)));
+}
+
+// One warp per block of B = 64 outcomes (two per lane); B < 64 (n < 6): one block, lane
+// l takes outcome l.
 template <typename C>
 __global__ void block_sums(const C *__restrict__ psi, unsigned long long nb, uint32_t B,
-                           double *__restrict__ S) {
-    for (unsigned long long b = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; b < nb;
-         b += (unsigned long long)gridDim.x * blockDim.x) {
-        double c = 0.0;
-        for (uint32_t j = 0; j < B; ++j) c = __dadd_rn(c, sprob(psi, b * B + j));
-        S[b] = c;
-    }
-}
-
-__global__ void chunk_scan(const double *__restrict__ S, unsigned long long nc, uint32_t C,
-                           double *__restrict__ L, double *__restrict__ tot) {
-    for (unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; c < nc;
-         c += (unsigned long long)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (uint32_t j = 0; j < C; ++j) {
-            L[c * C + j] = acc;
-            acc = __dadd_rn(acc, S[c * C + j]);
+                           unsigned long long *__restrict__ S) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const unsigned long long wid = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+    for (unsigned long long b = wid; b < nb; b += nw) {
+        unsigned long long s = 0;
+        if (B == 64) {
+            s = pfix(psi, b * 64 + 2 * lane) + pfix(psi, b * 64 + 2 * lane + 1);
+        } else {
+            if (lane < B) s = pfix(psi, lane);
+            if (lane + 32 < B) s += pfix(psi, lane + 32);
         }
-        tot[c] = acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) S[b] = s;
     }
 }
 
-// one thread: O_c and T (written at O[nc])
-__global__ void chunk_offsets(const double *__restrict__ tot, unsigned long long nc, double *O) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double acc = 0.0;
-    for (unsigned long long c = 0; c < nc; ++c) {
-        O[c] = acc;
-        acc = __dadd_rn(acc, tot[c]);
+// Chunk c of C = SCAN_THREADS x SCAN_ITEMS blocks (or all nb < C): exclusive prefix L of
+// its S and its total tot[c], by a shared-memory scan (the sums are exact integers, so
+// the order does not matter).
+__global__ void __launch_bounds__(SCAN_THREADS) chunk_scan(const unsigned long long *__restrict__ S,
+                                                           unsigned long long nb, uint32_t C,
+                                                           unsigned long long *__restrict__ L,
+                                                           unsigned long long *__restrict__ tot) {
+    __shared__ unsigned long long part[SCAN_THREADS];
+    const unsigned long long c = blockIdx.x;
+    const unsigned long long base = c * C;
+    const uint32_t t = threadIdx.x;
+    unsigned long long v[SCAN_ITEMS];
+    unsigned long long s = 0;
+#pragma unroll
+    for (uint32_t i = 0; i < SCAN_ITEMS; ++i) {
+        const unsigned long long j = base + (unsigned long long)t * SCAN_ITEMS + i;
+        v[i] = (t * SCAN_ITEMS + i < C && j < nb) ? S[j] : 0ull;
+        s += v[i];
     }
-    O[nc] = acc;
+    part[t] = s;
+    __syncthreads();
+    for (uint32_t o = 1; o < SCAN_THREADS; o <<= 1) {          // inclusive Hillis-Steele
+        const unsigned long long add = t >= o ? part[t - o] : 0ull;
+        __syncthreads();
+        part[t] += add;
+        __syncthreads();
+    }
+    unsigned long long run = t ? part[t - 1] : 0ull;            // exclusive
+#pragma unroll
+    for (uint32_t i = 0; i < SCAN_ITEMS; ++i) {
+        const unsigned long long j = base + (unsigned long long)t * SCAN_ITEMS + i;
+        if (t * SCAN_ITEMS + i < C && j < nb) L[j] = run;
+        run += v[i];
+    }
+    if (t == SCAN_THREADS - 1) tot[c] = part[t];
+}
+
+// One block: O_c = exclusive prefix of the chunk totals, and T at O[nc].
+__global__ void __launch_bounds__(1024) chunk_offsets(const unsigned long long *__restrict__ tot,
+                                                      unsigned long long nc,
+                                                      unsigned long long *__restrict__ O) {
+    __shared__ unsigned long long part[1024];
+    __shared__ unsigned long long carry;
+    const uint32_t t = threadIdx.x;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (unsigned long long c0 = 0; c0 < nc; c0 += 1024) {
+        const unsigned long long j = c0 + t;
+        const unsigned long long x = j < nc ? tot[j] : 0ull;
+        part[t] = x;
+        __syncthreads();
+        for (uint32_t o = 1; o < 1024; o <<= 1) {
+            const unsigned long long add = t >= o ? part[t - o] : 0ull;
+            __syncthreads();
+            part[t] += add;
+            __syncthreads();
+        }
+        if (j < nc) O[j] = carry + part[t] - x;
+        __syncthreads();
+        if (t == 0) carry += part[1023];
+        __syncthreads();
+    }
+    if (t == 0) O[nc] = carry;
 }
 
 template <typename C>
-__global__ void draw_shots(const C *__restrict__ psi, const double *__restrict__ S,
-                           const double *__restrict__ L, const double *__restrict__ O,
-                           unsigned long long nb, uint32_t B, uint32_t Cb, unsigned long long nc,
-                           unsigned long long seed, unsigned long long nshots,
-                           unsigned long long *__restrict__ out) {
-    const double T = O[nc];
+__global__ void draw_shots(const C *__restrict__ psi, const unsigned long long *__restrict__ L,
+                           const unsigned long long *__restrict__ O, unsigned long long nb, uint32_t B,
+                           uint32_t Cb, unsigned long long nc, unsigned long long seed,
+                           unsigned long long nshots, unsigned long long *__restrict__ out) {
+    const unsigned long long T = O[nc];
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
          i < nshots; i += (unsigned long long)gridDim.x * blockDim.x) {
         const unsigned long long z = splitmix64(seed + (i + 1) * SM_GAMMA);
-        const double u = __dmul_rn(__ull2double_rn(z >> 11), 0x1p-53);   // exact
-        const double target = __dmul_rn(u, T);
+        const unsigned long long target = __umul64hi((z >> 11) << 11, T);   // floor(u53 T / 2^53)
         // the largest b with P_b <= target (P_0 = 0 <= target)
         unsigned long long lo = 0, hi = nb - 1;
         while (lo < hi) {
             const unsigned long long mid = lo + (hi - lo + 1) / 2;
-            const double P = __dadd_rn(O[mid / Cb], L[mid]);
-            if (P <= target) lo = mid;
+            if (O[mid / Cb] + L[mid] <= target) lo = mid;
             else hi = mid - 1;
         }
-        unsigned long long b = lo;
-        while (S[b] == 0.0 && b > 0) --b;        // the first block with S_b > 0 has P_b = 0
-        const double r = __dsub_rn(target, __dadd_rn(O[b / Cb], L[b]));
-        double c = 0.0;
-        long long k = -1, last_nz = -1;
+        const unsigned long long b = lo;
+        const unsigned long long r = target - (O[b / Cb] + L[b]);   // < S_b
+        unsigned long long c = 0;
+        uint32_t k = B - 1;
         for (uint32_t j = 0; j < B; ++j) {
-            const double p = sprob(psi, b * B + j);
-            if (p > 0.0) last_nz = j;
-            c = __dadd_rn(c, p);
+            c += pfix(psi, b * B + j);
             if (c > r) {
                 k = j;
                 break;
             }
         }
-        if (k < 0) {
-            // running sum never exceeded r (rounding at the block's end): its last outcome
-            // with p > 0
-            for (uint32_t j = B; j-- > 0;)
-                if (sprob(psi, b * B + j) > 0.0) { last_nz = j; break; }
-            k = last_nz < 0 ? (long long)B - 1 : last_nz;
-        }
-        out[i] = b * B + (unsigned long long)k;
+        out[i] = b * B + k;
     }
 }
 
@@ -135,51 +199,51 @@ extern "C" sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64
     const unsigned long long N = 1ull << s->n;
     const uint32_t B = (uint32_t)std::min<unsigned long long>(64, N);
     const unsigned long long nb = N / B;
-    const uint32_t Cb = (uint32_t)std::min<unsigned long long>(4096, nb);
-    const unsigned long long nc = nb / Cb;
-    double *S = nullptr, *L = nullptr, *tot = nullptr, *O = nullptr;
-    unsigned long long *dout = nullptr;
+    const uint32_t Cb = (uint32_t)std::min<unsigned long long>(svk::SCAN_THREADS * svk::SCAN_ITEMS, nb);
+    const unsigned long long nc = (nb + Cb - 1) / Cb;
+    unsigned long long *S = nullptr, *L = nullptr, *tot = nullptr, *O = nullptr, *dout = nullptr;
     cudaStream_t st = s->stream;
-    SV_CUDA(cudaMallocAsync(&S, nb * sizeof(double), st));
+    SV_CUDA(cudaMallocAsync(&S, nb * sizeof(unsigned long long), st));
     sv_status rc = SV_OK;
     auto fail = [&](cudaError_t e, const char *what) {
         if (rc == SV_OK && e != cudaSuccess)
             rc = set_error(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA,
                            std::string("sv_sample: ") + what + ": " + cudaGetErrorString(e));
     };
-    fail(cudaMallocAsync(&L, nb * sizeof(double), st), "alloc");
-    fail(cudaMallocAsync(&tot, nc * sizeof(double), st), "alloc");
-    fail(cudaMallocAsync(&O, (nc + 1) * sizeof(double), st), "alloc");
+    fail(cudaMallocAsync(&L, nb * sizeof(unsigned long long), st), "alloc");
+    fail(cudaMallocAsync(&tot, nc * sizeof(unsigned long long), st), "alloc");
+    fail(cudaMallocAsync(&O, (nc + 1) * sizeof(unsigned long long), st), "alloc");
     if (!out_on_device) fail(cudaMallocAsync(&dout, nshots * sizeof(unsigned long long), st), "alloc");
     if (rc == SV_OK) {
-        const int grid = s->num_sms * 8;
+        const unsigned grid = (unsigned)std::min<unsigned long long>((nb * 32 + 255) / 256,
+                                                                     (unsigned long long)s->num_sms * 8);
         if (s->dtype == SV_C64)
             svk::block_sums<<<grid, 256, 0, st>>>(reinterpret_cast<const float2 *>(s->buf), nb, B, S);
         else
             svk::block_sums<<<grid, 256, 0, st>>>(reinterpret_cast<const double2 *>(s->buf), nb, B, S);
         fail(cudaGetLastError(), "block sums");
-        svk::chunk_scan<<<(unsigned)std::min<unsigned long long>((nc + 127) / 128, 65535), 128, 0, st>>>(
-            S, nc, Cb, L, tot);
+        svk::chunk_scan<<<(unsigned)nc, svk::SCAN_THREADS, 0, st>>>(S, nb, Cb, L, tot);
         fail(cudaGetLastError(), "chunk scan");
-        svk::chunk_offsets<<<1, 32, 0, st>>>(tot, nc, O);
+        svk::chunk_offsets<<<1, 1024, 0, st>>>(tot, nc, O);
         fail(cudaGetLastError(), "chunk offsets");
     }
-    double T = 0.0;
+    unsigned long long T = 0;
     if (rc == SV_OK) {
-        fail(cudaMemcpyAsync(&T, O + nc, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+        fail(cudaMemcpyAsync(&T, O + nc, sizeof(T), cudaMemcpyDeviceToHost, st), "copy");
         fail(cudaStreamSynchronize(st), "sync");
-        if (rc == SV_OK && !(T > 0.0)) rc = set_error(SV_ERR_STATE, "sv_sample: the state has zero norm");
+        if (rc == SV_OK && T == 0)
+            rc = set_error(SV_ERR_STATE, "sv_sample: the state has no probability mass to sample");
     }
     if (rc == SV_OK) {
         unsigned long long *dst = out_on_device ? reinterpret_cast<unsigned long long *>(out) : dout;
         const unsigned grid = (unsigned)std::min<unsigned long long>((nshots + 255) / 256,
                                                                      (unsigned long long)s->num_sms * 32);
         if (s->dtype == SV_C64)
-            svk::draw_shots<<<grid, 256, 0, st>>>(reinterpret_cast<const float2 *>(s->buf), S, L, O, nb,
-                                                  B, Cb, nc, seed, nshots, dst);
+            svk::draw_shots<<<grid, 256, 0, st>>>(reinterpret_cast<const float2 *>(s->buf), L, O, nb, B,
+                                                  Cb, nc, seed, nshots, dst);
         else
-            svk::draw_shots<<<grid, 256, 0, st>>>(reinterpret_cast<const double2 *>(s->buf), S, L, O, nb,
-                                                  B, Cb, nc, seed, nshots, dst);
+            svk::draw_shots<<<grid, 256, 0, st>>>(reinterpret_cast<const double2 *>(s->buf), L, O, nb, B,
+                                                  Cb, nc, seed, nshots, dst);
         fail(cudaGetLastError(), "shots");
         if (!out_on_device && rc == SV_OK)
             fail(cudaMemcpyAsync(out, dout, nshots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
