@@ -230,8 +230,9 @@ sv_status sv_density_probs(sv_state *s, void *out, int out_on_device);
  * u = SplitMix64(seed + (i+1) * 0x9E3779B97F4A7C15) >> 11 (53 bits), target =
  * floor(u T / 2^53); the outcome is the k with C_{k-1} <= target < C_k.  Outcomes with
  * P_k = 0 are never drawn.  Valid for states of norm below 64 (the sums stay below 2^64).
- * out: nshots uint64 (host or device memory per out_on_device).  Temporary device memory:
- * 2^n / 4 bytes.  SV_ERR_STATE if T = 0 (a zero state).  Synchronises for host output. */
+ * out: nshots uint64 (host or device memory per out_on_device).  Scratch device memory:
+ * 2^n / 4 bytes (plus 8 bytes per shot for host output), kept by the state for the next
+ * call and released by sv_free.  SV_ERR_STATE if T = 0 (a zero state).  Synchronises. */
 sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64_t *out, int out_on_device);
 /* The min(k, 2^n) most probable outcomes (1 <= k <= 64), sorted by probability
  * descending, ties to the lower index.  idx/p are host arrays of k entries.  Synchronises. */

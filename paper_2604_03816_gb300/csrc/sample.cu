@@ -17,7 +17,8 @@
 //    outcome is the block's first k whose running sum of P exceeds target - P_b.
 //
 // Step 3 reads the state once (coalesced, integer work only for complex64; complex128
-// computes p_k on the FP64 pipe); each shot reads one block of the state.
+// computes p_k on the FP64 pipe); each shot reads one block of the state.  The scratch
+// arrays stay allocated in the state between calls (2^n / 4 bytes plus the shots).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,25 +69,50 @@ __device__ __forceinline__ unsigned long long pfix(const double2 *psi, unsigned 
     return fixed_of(__dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)));
 }
 
-// One warp per block of B = 64 outcomes (two per lane); B < 64 (n < 6): one block, lane
-// l takes outcome l.
+// P of the two adjacent amplitudes 2j, 2j + 1 (one 16-byte load for complex64).
+__device__ __forceinline__ unsigned long long pfix2(const float2 *psi, unsigned long long j) {
+    const float4 v = reinterpret_cast<const float4 *>(psi)[j];
+    return fixed_of(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y))) +
+           fixed_of(__fadd_rn(__fmul_rn(v.z, v.z), __fmul_rn(v.w, v.w)));
+}
+__device__ __forceinline__ unsigned long long pfix2(const double2 *psi, unsigned long long j) {
+    return pfix(psi, 2 * j) + pfix(psi, 2 * j + 1);
+}
+
+// One warp per block of B = 64 outcomes (two adjacent ones per lane), four blocks in
+// flight per warp; B < 64 (n < 6): one block, lane l takes outcomes l and l + 32.
 template <typename C>
 __global__ void block_sums(const C *__restrict__ psi, unsigned long long nb, uint32_t B,
                            unsigned long long *__restrict__ S) {
+    constexpr int ILP = 4;
     const uint32_t lane = threadIdx.x & 31u;
     const unsigned long long wid = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-    for (unsigned long long b = wid; b < nb; b += nw) {
-        unsigned long long s = 0;
-        if (B == 64) {
-            s = pfix(psi, b * 64 + 2 * lane) + pfix(psi, b * 64 + 2 * lane + 1);
-        } else {
+    if (B < 64) {
+        if (wid == 0) {
+            unsigned long long s = 0;
             if (lane < B) s = pfix(psi, lane);
             if (lane + 32 < B) s += pfix(psi, lane + 32);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) S[0] = s;
+        }
+        return;
+    }
+    for (unsigned long long b0 = wid; b0 < nb; b0 += ILP * nw) {
+        unsigned long long s[ILP];
+#pragma unroll
+        for (int u = 0; u < ILP; ++u) {
+            const unsigned long long b = b0 + (unsigned long long)u * nw;
+            s[u] = b < nb ? pfix2(psi, b * 32 + lane) : 0ull;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) S[b] = s;
+        for (int u = 0; u < ILP; ++u) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s[u] += __shfl_xor_sync(0xffffffffu, s[u], o);
+            const unsigned long long b = b0 + (unsigned long long)u * nw;
+            if (lane == 0 && b < nb) S[b] = s[u];
+        }
     }
 }
 
@@ -201,22 +227,29 @@ extern "C" sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64
     const unsigned long long nb = N / B;
     const uint32_t Cb = (uint32_t)std::min<unsigned long long>(svk::SCAN_THREADS * svk::SCAN_ITEMS, nb);
     const unsigned long long nc = (nb + Cb - 1) / Cb;
-    unsigned long long *S = nullptr, *L = nullptr, *tot = nullptr, *O = nullptr, *dout = nullptr;
     cudaStream_t st = s->stream;
-    SV_CUDA(cudaMallocAsync(&S, nb * sizeof(unsigned long long), st));
     sv_status rc = SV_OK;
     auto fail = [&](cudaError_t e, const char *what) {
         if (rc == SV_OK && e != cudaSuccess)
             rc = set_error(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA,
                            std::string("sv_sample: ") + what + ": " + cudaGetErrorString(e));
     };
-    fail(cudaMallocAsync(&L, nb * sizeof(unsigned long long), st), "alloc");
-    fail(cudaMallocAsync(&tot, nc * sizeof(unsigned long long), st), "alloc");
-    fail(cudaMallocAsync(&O, (nc + 1) * sizeof(unsigned long long), st), "alloc");
-    if (!out_on_device) fail(cudaMallocAsync(&dout, nshots * sizeof(unsigned long long), st), "alloc");
+    // scratch S, L, tot, O (and the shots for host output), kept in the state across calls
+    const size_t words = 2 * nb + 2 * nc + 1 + (out_on_device ? 0 : nshots);
+    if (s->samp_cap < words * sizeof(unsigned long long)) {
+        SV_CUDA(cudaStreamSynchronize(st));
+        if (s->samp) cudaFree(s->samp);
+        s->samp = nullptr;
+        s->samp_cap = 0;
+        SV_CUDA(cudaMalloc(&s->samp, words * sizeof(unsigned long long)));
+        s->samp_cap = words * sizeof(unsigned long long);
+    }
+    unsigned long long *S = static_cast<unsigned long long *>(s->samp);
+    unsigned long long *L = S + nb, *tot = L + nb, *O = tot + nc;
+    unsigned long long *dout = out_on_device ? nullptr : O + nc + 1;
     if (rc == SV_OK) {
         const unsigned grid = (unsigned)std::min<unsigned long long>((nb * 32 + 255) / 256,
-                                                                     (unsigned long long)s->num_sms * 8);
+                                                                     (unsigned long long)s->num_sms * 16);
         if (s->dtype == SV_C64)
             svk::block_sums<<<grid, 256, 0, st>>>(reinterpret_cast<const float2 *>(s->buf), nb, B, S);
         else
@@ -249,11 +282,6 @@ extern "C" sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64
             fail(cudaMemcpyAsync(out, dout, nshots * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st),
                  "copy");
     }
-    cudaFreeAsync(S, st);
-    if (L) cudaFreeAsync(L, st);
-    if (tot) cudaFreeAsync(tot, st);
-    if (O) cudaFreeAsync(O, st);
-    if (dout) cudaFreeAsync(dout, st);
     if (rc != SV_OK) return rc;
     if (!out_on_device) return check_device_error(s);
     return SV_OK;

@@ -128,6 +128,7 @@ sv_status sv_free(sv_state *s) {
     if (s->owned && s->buf) cudaFree(s->buf);
     if (s->ws) cudaFree(s->ws);
     if (s->snap) cudaFree(s->snap);
+    if (s->samp) cudaFree(s->samp);
     delete s;
     return SV_OK;
 }

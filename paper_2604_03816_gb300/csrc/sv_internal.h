@@ -99,6 +99,8 @@ struct sv_state {
     size_t snap_cap = 0;
     int num_sms = 0;
     uint32_t policy = 0;        // SV_POLICY_* flags (kernel selection)
+    void *samp = nullptr;       // sampling scratch (sample.cu), kept across calls
+    size_t samp_cap = 0;
 };
 
 // One batched launch: gate k/t applied to `states` consecutive states at psi with
