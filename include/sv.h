@@ -121,6 +121,7 @@ sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device);
 /* DAG-based gate fusion, Section 5.1-5.2 (Eq. 8 DAG, Algorithm 2, Eq. 9 product).
  * Gates fuse along DAG edges while the union of their qubits has at most max_k
  * members and contracting the edge keeps the DAG acyclic; U_fused = U_v . U_u in FP64.
+ * A vertex's predecessors are tried narrowest union first (ties by gate index).
  * max_k = 0 returns the gates unfused.  Sweeps repeat in min-id topological order
  * until nothing changes; the result is deterministic.  Fused targets are sorted
  * ascending.  Gates wider than max_k are kept as they are (k <= SV_MAX_K).

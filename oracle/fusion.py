@@ -20,7 +20,9 @@ Readings where the paper is silent or ambiguous (each one is listed in the design doc
 * Topological order: Kahn's algorithm that always takes the ready vertex with the
   smallest id.  A vertex starts with its gate's index as id; a fused vertex keeps the
   id of u, the predecessor that absorbed v.
-* Predecessors of v are tried in ascending id order.
+* Predecessors of v are tried in ascending order of |q(u) | q(v)| (the narrowest fused
+  gate first, which leaves room for later contractions), ties by ascending id.  The
+  paper's loop over "each predecessor" leaves the order open.
 * A fused gate's qubits are sorted ascending and each factor is embedded on the union
   with identities on the other qubits before the product.
 * q_max^fuse = 0 means no fusion: the gates come back unchanged (targets sorted).
@@ -41,7 +43,7 @@ analysis and names it as future work, Sections 10-11):
   vertices that share a qubit with v, are placed before v in the sweep's topological
   order and are not its predecessors, in ascending id, contracting one when there is no
   path from it to v (the two commute, so U_fused = U_v . U_u is the product in either
-  order).
+  order); both groups in the same order as the predecessors above.
 """
 from __future__ import annotations
 
@@ -215,10 +217,13 @@ def fuse(gates: Sequence[Tuple[Sequence[int], np.ndarray]], n: int, qmax: int,
         for v in order:
             if v not in dag.preds:            # absorbed earlier in this sweep
                 continue
-            cands = sorted(dag.preds[v])
+            def width_then_id(u):
+                return (len(set(dag.q[u]) | set(dag.q[v])), u)
+            cands = sorted(dag.preds[v], key=width_then_id)
             if commute:
-                cands += sorted(w for w in dag.preds if w != v and w not in dag.preds[v]
-                                and pos[w] < pos[v] and set(dag.q[w]) & set(dag.q[v]))
+                cands += sorted((w for w in dag.preds if w != v and w not in dag.preds[v]
+                                 and pos[w] < pos[v] and set(dag.q[w]) & set(dag.q[v])),
+                                key=width_then_id)
             for u in cands:
                 if len(set(dag.q[u]) | set(dag.q[v])) > qmax:
                     continue

@@ -6,7 +6,9 @@
 //
 // Sweeps: until a sweep fuses nothing, take the vertices in topological order (Kahn's
 // algorithm, smallest vertex id first); for each surviving vertex v try its
-// predecessors u in ascending id order and fuse the first u with
+// predecessors u -- narrowest union |q(u) U q(v)| first, ties by ascending id (the
+// paper leaves the order open; narrow fused gates leave room for later contractions)
+// -- and fuse the first u with
 //   |q(u) U q(v)| <= max_k   and   no directed path u -> ... -> v other than (u, v),
 // i.e. the contraction keeps the graph acyclic, which is how Algorithm 2's "u is the
 // sole predecessor of v on the shared qubits" is read here (it also excludes detours
@@ -277,9 +279,22 @@ std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t m
         dag.set_positions(order);
         for (int v : order) {
             if (!dag.nodes_[v].alive) continue;
+            // candidates: predecessors, then (commute) siblings, each group by (width, id)
+            auto by_width = [&](std::vector<int> &c) {
+                std::vector<std::pair<uint32_t, int>> w;
+                w.reserve(c.size());
+                for (int u : c) {
+                    uint32_t qs[2 * SV_MAX_K];
+                    w.emplace_back(Dag::union_qubits(dag.nodes_[u].g, dag.nodes_[v].g, qs), u);
+                }
+                std::sort(w.begin(), w.end());
+                for (size_t i = 0; i < c.size(); ++i) c[i] = w[i].second;
+            };
             std::vector<int> cands(dag.nodes_[v].preds.begin(), dag.nodes_[v].preds.end());
+            by_width(cands);
             if (commute) {
-                const std::vector<int> sib = dag.siblings(v);
+                std::vector<int> sib = dag.siblings(v);
+                by_width(sib);
                 cands.insert(cands.end(), sib.begin(), sib.end());
             }
             for (int u : cands) {
