@@ -44,8 +44,8 @@ KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
             "sha256_prefix": "2c8c524322c9a611", "n": 30,
             "bytes_per_launch": (1.073810e9 + 1.014305e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 72.7% of GPU time, all apply kernels "
-                      "97.2% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 82.6% of GPU time, all apply kernels "
+                      "97.1% (profiles/fused_pass_grid30q_k5_launches.md)",
             "traffic_source": "apply_tc<5,0,2> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
