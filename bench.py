@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--cycles", type=int, default=24)
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-unfused", action="store_true",
                     help="also time the unfused complex128 per-gate form once")
@@ -721,16 +721,27 @@ def main():
             states = [state, sv.sv_alloc(args.n, dt, stream=streams[1])]
             torch.cuda.synchronize()
 
+            import threading
+            first_in = threading.Event()
+
             def worker(w, nsteps):
                 st, out = states[w], h_outs[w].numpy()
+                # the second state starts once the first one's input is in: started
+                # together, the two would move in lockstep (both uploading, then both
+                # computing at half speed) and no transfer would overlap a pass
+                if w == 1:
+                    first_in.wait()
                 with torch.cuda.stream(streams[w]):
                     for _ in range(nsteps):
                         if sv.sv_info(st)[1] != dt:
                             sv.sv_set_dtype(st, dt)
                         sv.sv_set_state(st, h_in_np)
+                        if w == 0:
+                            first_in.set()
                         c = sv.sv_fuse(gates, args.n, args.k)
                         sv.sv_apply_circuit(st, c, adaptive=True)
                         sv.sv_probs(st, out)
+                first_in.set()
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(streams[0])
             streams[1].wait_event(f0)
