@@ -42,18 +42,21 @@
 
 namespace svk {
 
-struct Tc64 {
+// SUB: MMA subtiles (128 groups each) per TMA stage.  SUB = 2 doubles the contiguous
+// segments of launches whose targets sit above the low index bits (4 KiB instead of 2).
+template <int SUB = 1>
+struct Tc64S {
     static constexpr uint32_t K = 4;
     static constexpr uint32_t D = 16;                     // amplitudes per group
     static constexpr uint32_t KD = 32;                    // real K = N
-    static constexpr uint32_t ROWS = 128;                 // groups per tile (MMA M)
-    static constexpr uint32_t TB = 11;                    // tile bits
-    static constexpr uint32_t TILE_BYTES = ROWS * D * 16u;    // 32 KB
+    static constexpr uint32_t ROWS = 128;                 // groups per MMA subtile (MMA M)
+    static constexpr uint32_t TB = 11 + (SUB == 2 ? 1u : 0u);   // tile bits
+    static constexpr uint32_t TILE_BYTES = SUB * ROWS * D * 16u;  // 32 or 64 KB
     static constexpr uint32_t B_BYTES = KD * KD * 2u;     // one FP16 digit slice of R
     static constexpr uint32_t NB = 12;                    // B_j and B_j 2^-9, j = 0..5
     static constexpr uint32_t SBO = (KD / 8u) * 128u;
-    static constexpr uint32_t NS = 4;                     // raw stages
-    static constexpr uint32_t NOUT = 2;                   // output staging tiles
+    static constexpr uint32_t NS = SUB == 2 ? 2u : 4u;    // raw stages
+    static constexpr uint32_t NOUT = SUB == 2 ? 1u : 2u;  // output staging tiles
     static constexpr uint32_t NACC = 5;                   // D0, D1, D2, D3, D45
     static constexpr uint32_t ACC = NACC * KD;            // TMEM columns of one D set
     static constexpr uint32_t A_COLS = KD / 2u;           // TMEM columns of one A digit slice
@@ -68,6 +71,7 @@ struct Tc64 {
     // warps 0-7 transform, 8 producer, 9 MMA issuer, 10-17 epilogue
     static constexpr uint32_t W_PROD = 8, W_MMA = 9, W_EPI = 10;
 };
+using Tc64 = Tc64S<1>;
 
 struct Tc64Args {
     int16_t b[6][32 * 32];   // digits of R (row-major n x kk), most significant first
@@ -139,10 +143,11 @@ __device__ __forceinline__ double combine_levels(float f0, float f1, float f2, f
 }
 
 // XP: the launch has targets among tile bits 0..2 and takes members in the lane's XOR
-// order; otherwise no permutation code at all.
-template <bool XP>
+// order; otherwise no permutation code at all.  The pipelines count tiles (j: raw stage,
+// output staging) and MMA subtiles (js = j SUB + sub: A and D buffers, row exponents).
+template <bool XP, int SUB = 1>
 __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc64Args a) {
-    using S = Tc64;
+    using S = Tc64S<SUB>;
     constexpr uint32_t KD = S::KD, NS = S::NS, NOUT = S::NOUT;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) unsigned long long full[NS], empty[NS];
@@ -235,9 +240,10 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(S::ROWS, KD);
             const uint32_t B0 = smem_u32(sB);
-            uint32_t j = 0;
-            for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
-                const uint32_t b = j & 1u, u = j >> 1;
+            const unsigned long long nsub = a.ntiles > first
+                                                ? ((a.ntiles - first + step - 1) / step) * SUB : 0;
+            for (unsigned long long js = 0; js < nsub; ++js) {
+                const uint32_t b = (uint32_t)js & 1u, u = (uint32_t)(js >> 1);
                 if (!mbar_wait_or_abort(smem_u32(&a_full[b]), u & 1u, abort)) break;
                 if (!mbar_wait_or_abort(smem_u32(&d_empty[b]), (u & 1u) ^ 1u, abort)) break;
                 tc_fence_after();
@@ -274,17 +280,21 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         // the code small (the roles run different code on every SM sub-partition).
         const uint32_t row = (warp & 3u) * 32u + lane;
         const uint32_t part = warp >> 2;
-        const uint32_t gbase = group_base(row);
         const uint32_t lo_off[4] = {0u, 1u << a.lp[0], 1u << a.lp[1], (1u << a.lp[0]) | (1u << a.lp[1])};
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         const uint32_t cx = ((xl & 1u) << a.lp[0]) | (((xl >> 1) & 1u) << a.lp[1]);
         uint32_t j = 0;
-        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
+        bool stop = false;
+        for (unsigned long long t = first; t < a.ntiles && !stop; t += step, ++j) {
             const uint32_t s = j % NS;
-            bool ok = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
-            const uint32_t ab = j & 1u;
-            ok = ok && mbar_wait_or_abort(smem_u32(&a_empty[ab]), ((j >> 1) & 1u) ^ 1u, abort);
+            const bool okf = mbar_wait_or_abort(smem_u32(&full[s]), (j / NS) & 1u, abort);
             const double2 *rs = reinterpret_cast<const double2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
+#pragma unroll 1
+          for (uint32_t sub = 0; sub < (uint32_t)SUB; ++sub) {
+            const uint32_t js = j * SUB + sub;
+            const uint32_t gbase = group_base(sub * S::ROWS + row);
+            const uint32_t ab = js & 1u;
+            const bool ok = okf && mbar_wait_or_abort(smem_u32(&a_empty[ab]), ((js >> 1) & 1u) ^ 1u, abort);
             // the row's largest exponent field: each half over its members (high words)
             uint32_t em = 0;                      // largest |high word|: its exponent field
 #pragma unroll
@@ -294,10 +304,13 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
                 em = max(em, max(w[1] & 0x7FFFFFFFu, w[3] & 0x7FFFFFFFu));
             }
             emax_part[part][row] = max(em >> 20, 1u);
-            if (!named_bar_and(1, 256, ok)) break;
+            if (!named_bar_and(1, 256, ok)) { stop = true; break; }
             tc_fence_after();
             const uint32_t emax = max(emax_part[0][row], emax_part[1][row]);
-            if (part == 0) row_exp[j & 3u][row] = (int)emax;
+            // slot js & 3 was last read by the epilogue of subtile js - 4, which finished
+            // before the MMAs of subtile js - 2 were issued, whose completion released
+            // a_empty[ab]
+            if (part == 0) row_exp[js & 3u][row] = (int)emax;
             const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + (((warp & 3u) * 32u) << 16);
 #pragma unroll 1
             for (uint32_t c0 = part * 8u; c0 < part * 8u + 8u; c0 += 4) {
@@ -324,12 +337,13 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
             fence_proxy_async_smem();             // reads of the raw stage before its refill
             tmem_wait_st();
             tc_fence_before();
-            named_bar(1, 256);                    // also: emax_part is free for the next tile
+            named_bar(1, 256);                    // also: emax_part is free for the next subtile
             if (tid == 0) {
-                mbar_arrive(smem_u32(&empty[s]));
+                if (sub == (uint32_t)SUB - 1u) mbar_arrive(smem_u32(&empty[s]));
                 mbar_arrive(smem_u32(&a_full[ab]));
-                mbar_arrive(smem_u32(&scale_full[j & 3u]));
+                mbar_arrive(smem_u32(&scale_full[js & 3u]));
             }
+          }
         }
     } else if (warp >= S::W_EPI) {
         // ------------------------------------------------------------ epilogue
@@ -338,23 +352,29 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         const uint32_t row = quad * 32u + lane;
         const uint32_t et = tid - S::W_EPI * 32u;    // 0..255
         const uint32_t part = et >> 7;
-        const uint32_t gbase = group_base(row);
         const uint32_t lo_off[4] = {0u, 1u << a.lp[0], 1u << a.lp[1], (1u << a.lp[0]) | (1u << a.lp[1])};
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         const uint32_t cx = ((xl & 1u) << a.lp[0]) | (((xl >> 1) & 1u) << a.lp[1]);
         SegLanes sl;
         sl.init(a.L, a.h, a.hi, lane);
         uint32_t j = 0;
-        for (unsigned long long t = first; t < a.ntiles; t += step, ++j) {
-            const uint32_t b = j & 1u, ob = j % NOUT;
-            bool ok = mbar_wait_or_abort(smem_u32(&d_full[b]), (j >> 1) & 1u, abort);
-            ok = ok && mbar_wait_or_abort(smem_u32(&scale_full[j & 3u]), (j >> 2) & 1u, abort);
-            if (!named_bar_and(2, 256, ok)) break;
-            tc_fence_after();
-            if (et < 32) bulk_wait_read<(int)NOUT - 1>();
-            named_bar(2, 256);
-            const int p = row_exp[j & 3u][row] + a.b_exp - 1078;   // out = Z 2^p
+        bool stop = false;
+        for (unsigned long long t = first; t < a.ntiles && !stop; t += step, ++j) {
+            const uint32_t ob = j % NOUT;
             double2 *out = reinterpret_cast<double2 *>(smem + S::OFF_OUT + ob * S::TILE_BYTES);
+#pragma unroll 1
+          for (uint32_t sub = 0; sub < (uint32_t)SUB; ++sub) {
+            const uint32_t js = j * SUB + sub, b = js & 1u;
+            const uint32_t gbase = group_base(sub * S::ROWS + row);
+            bool ok = mbar_wait_or_abort(smem_u32(&d_full[b]), (js >> 1) & 1u, abort);
+            ok = ok && mbar_wait_or_abort(smem_u32(&scale_full[js & 3u]), (js >> 2) & 1u, abort);
+            if (!named_bar_and(2, 256, ok)) { stop = true; break; }
+            tc_fence_after();
+            if (sub == 0) {
+                if (et < 32) bulk_wait_read<(int)NOUT - 1>();   // this staging tile is free
+                named_bar(2, 256);
+            }
+            const int p = row_exp[js & 3u][row] + a.b_exp - 1078;   // out = Z 2^p
             const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16);
             // eight columns (four members) of the five accumulators per step
 #pragma unroll 1
@@ -380,6 +400,8 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
             fence_proxy_async_smem();
             named_bar(2, 256);
             if (et == 0) mbar_arrive(smem_u32(&d_empty[b]));
+          }
+            if (stop) break;
             if (et < 32) {
                 if (lane < nseg)
                     bulk_s2g(psi + sl.base(t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
@@ -398,14 +420,18 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
 
 sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
     using S = Tc64;
+    using S2 = Tc64S<2>;
     static std::once_flag once;
     static cudaError_t init_err = cudaSuccess;
     std::call_once(once, [] {
-        init_err = cudaFuncSetAttribute(apply_tc64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        init_err = cudaFuncSetAttribute(apply_tc64<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)S::SMEM);
         if (init_err == cudaSuccess)
-            init_err = cudaFuncSetAttribute(apply_tc64<true>,
+            init_err = cudaFuncSetAttribute(apply_tc64<true, 1>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (init_err == cudaSuccess)
+            init_err = cudaFuncSetAttribute(apply_tc64<false, 2>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S2::SMEM);
     });
     if (init_err != cudaSuccess)
         return svi::set_error(SV_ERR_CUDA, std::string("tensor-core kernel setup: ") +
@@ -416,7 +442,21 @@ sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
         gw = svi::widen_gate(g0, s->n, 4);
         g = &gw;
     }
-    const Plan p = make_plan(s->n, 4, g->t, S::TB);
+    Plan p = make_plan(s->n, 4, g->t, S::TB);
+    // 16-byte accesses: bank group = tile bits 0..2; the lowest targets there (at most
+    // two, the ones inside a group of four members) get a lane-dependent order
+    uint32_t tl = 0;
+    while (tl < 3u && p.lp[tl] < 3u) ++tl;
+    // without the member-order variant and with three or four targets above the low bits
+    // (segments of 4 KiB or less), two MMA subtiles per 64 KiB stage: measured at 30
+    // qubits, four high targets 11.26 -> 10.58 ms per pass, but two high targets 9.94 ->
+    // 10.47 ms, so the mode is kept for the short segments
+    const bool wide = std::min(tl, 2u) < 2u && s->n >= S2::TB && p.h >= 3;
+    if (wide) {
+        p = make_plan(s->n, 4, g->t, S2::TB);
+        tl = 0;
+        while (tl < 3u && p.lp[tl] < 3u) ++tl;
+    }
     Tc64Args a;
     // R (real embedding of U) and its six digits, exactly, on the host
     double rmax = 0.0;
@@ -441,16 +481,13 @@ sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
     a.h = p.h;
     for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
     for (int j = 0; j < 4; ++j) a.lp[j] = p.lp[j];
-    // 16-byte accesses: bank group = tile bits 0..2; the lowest targets there (at most
-    // two, the ones inside a group of four members) get a lane-dependent order
-    uint32_t tl = 0;
-    while (tl < 3u && p.lp[tl] < 3u) ++tl;
     a.xs = 3u - tl;
     a.xt = std::min(tl, 2u);
     const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
     // the permutation pays off from two targets in bits 0..2 (4-way conflicts and worse)
-    if (a.xt >= 2) apply_tc64<true><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
-    else apply_tc64<false><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    if (wide && a.xt < 2) apply_tc64<false, 2><<<grid, S2::THREADS, S2::SMEM, s->stream>>>(a);
+    else if (a.xt >= 2) apply_tc64<true, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    else apply_tc64<false, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }
