@@ -240,3 +240,26 @@ def test_commutation_fuse_like_checks_structure(svlib):
         svlib.sv_fuse_like(pattern, svlib.gates_from_specs(changed))
     with pytest.raises(svlib.SvError):
         svlib.sv_fuse_ex(svlib.gates_from_specs(specs), n, 3, 2)
+
+
+def test_new_entry_points_validate_arguments(svlib):
+    """Host-only argument checks of sv_gate_structure and sv_fuse_ex (no GPU call)."""
+    import ctypes
+    lib = ctypes.CDLL(svlib.LIB_PATH)
+    h = OG.matrix("h")
+    with pytest.raises(svlib.SvError):
+        svlib.sv_gate_structure((0, 0), np.eye(4))             # repeated target
+    with pytest.raises(svlib.SvError):
+        svlib.sv_gate_structure((0, 1, 2, 3, 4, 5), np.eye(64))  # wider than 5
+    assert lib.sv_gate_structure(None, None, None) != 0         # null gate
+    gl = [((0,), h), ((1,), h)]
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse_ex(gl, 2, 6, svlib.SV_FUSE_COMMUTE)      # max_k > 5
+    with pytest.raises(svlib.SvError):
+        svlib.sv_fuse_ex(gl, 1, 2, svlib.SV_FUSE_COMMUTE)      # target >= n
+    c = svlib.sv_fuse_ex(gl, 2, 0, svlib.SV_FUSE_COMMUTE)      # max_k = 0: unfused
+    assert len(c) == 2
+    # either output of sv_gate_structure may be NULL
+    ga = svlib.GateArray([((0, 1), OG.matrix("cz"))])
+    kind = ctypes.c_uint32()
+    assert lib.sv_gate_structure(ga.arr, ctypes.byref(kind), None) == 0 and kind.value == svlib.SV_STRUCT_DIAGONAL
