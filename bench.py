@@ -71,16 +71,23 @@ def parse():
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare-unfused", action="store_true",
-                    help="also time the unfused complex128 per-gate form once")
+    ap.add_argument("--no-compare-unfused", action="store_true",
+                    help="skip timing the unfused complex128 per-gate form of the circuit")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra lines of the default run (28-33 qubit configurations, "
+                         "complex128, batched and served summaries)")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--mode", default="single",
-                    choices=["single", "batched", "serve", "sample", "noise", "qft"],
+                    choices=["single", "batched", "serve", "sample", "noise", "qft", "shard"],
                     help="single: the 30-qubit hot path (default line); batched: 512 HEA "
                          "circuits of 16-22 qubits; serve: Poisson request stream; sample: "
                          "measurement shots from the 30-qubit circuit's output state; "
                          "qft: QFT of a basis state with structure-aware passes against "
-                         "the same schedule forced dense")
+                         "the same schedule forced dense; shard: one state over the "
+                         "ranks (global-qubit sharding, NCCL exchanges), --n qubits per GPU")
+    ap.add_argument("--emulate-ranks", type=int, default=0,
+                    help="shard: run this many ranks as threads on one GPU (exchanges are "
+                         "device copies) instead of one process per GPU")
     ap.add_argument("--shots", type=int, default=1 << 20, help="sample: shots per step")
     ap.add_argument("--circuit", default="qft", choices=["qft", "phase_heavy", "qaoa"],
                     help="qft mode: the circuit family (QFT; random diagonal-heavy; QAOA layers)")
@@ -91,7 +98,8 @@ def parse():
                     help="batched: fixed fusion width with whole-batch chunks (0: autotune)")
     ap.add_argument("--rates", default="10,30,100,300,1000,2000", help="serve: req/s list")
     ap.add_argument("--duration", type=float, default=4.0, help="serve: seconds per rate")
-    ap.add_argument("--max-requests", type=int, default=40, help="serve: requests per rate")
+    ap.add_argument("--requests", type=int, default=500,
+                    help="serve: requests per rate (arrivals over requests / rate seconds)")
     return ap.parse_args()
 
 
@@ -222,6 +230,7 @@ def run_reference(args):
     from oracle import gates as OG
     specs = W.grid_random(args.n, args.cycles)
     gl = OG.gate_list(specs)
+    nfused = len(oracle.fuse(gl, args.n, args.k))     # the same schedule length (Algorithm 2)
     psi = oracle.basis(args.n, 0)
     per_step = max(1, int(os.environ.get("REF_GATES_PER_STEP", "3")))
     times = []
@@ -242,7 +251,7 @@ def run_reference(args):
            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": config_dict(args, len(specs), None),
+           "config": config_dict(args, len(specs), nfused),
            "cpu_baseline": {"value": value, "unit": "circuits/s", "cores": cores,
                             "kind": "oracle",
                             "sample": f"{per_step} gates per step of the {args.n}-qubit "
@@ -445,20 +454,18 @@ def run_qft(args):
     print(json.dumps(out), flush=True)
 
 
-def run_serve(args):
-    """Poisson arrivals (each rate in --rates) of seeded brickwork circuits, width
-    U{10..30}, depth U{10..60}, 70% complex64 / 30% complex128, top-64 outcomes, under a
-    150 GiB HBM budget; at most --max-requests per rate.  Latency = server clock from
-    submission to the result being ready."""
-    import torch
-    from paper_2604_03816_gb300 import sv
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
+def serve_rates(sv, rates, n_requests, budget_gib=150, slots=16, max_k=4):
+    """Poisson arrivals of seeded brickwork circuits (width U{10..30}, depth U{10..60}, 70%
+    complex64 / 30% complex128, top-64 outcomes) at each offered rate, n_requests arrivals
+    per rate (an arrival window of n_requests / rate seconds), through one server per rate
+    under the HBM budget.  Latency = the server's clock from submission to the result.
+    Above the server's capacity the queue grows over the window, so p50/p99 there describe
+    a burst of n_requests, not a steady state; the achieved circuits/s is the capacity."""
     per_rate = []
-    for rate in [float(r) for r in args.rates.split(",")]:
-        reqs = W.serving_stream(rate, args.duration)[: args.max_requests]
+    for rate in rates:
+        reqs = W.serving_stream(rate, 1e9, max_requests=n_requests)
         arrays = [sv.GateArray(sv.gates_from_specs(r.gates)) for r in reqs]
-        srv = sv.sv_server_create(budget_bytes=150 << 30, max_slots=16, max_k=4)
+        srv = sv.sv_server_create(budget_bytes=budget_gib << 30, max_slots=slots, max_k=max_k)
         t0 = time.perf_counter()
         ids = {}
         got = {}
@@ -477,10 +484,23 @@ def run_serve(args):
         last = max(got[i]["t_done"] for i in ids)
         ok = sum(1 for i in ids if got[i]["status"] == 0)
         per_rate.append({"rate_hz": rate, "requests": len(ids), "ok": ok,
+                         "arrival_window_s": reqs[-1].arrival_s,
                          "p50_ms": 1000 * float(np.percentile(lat, 50)),
                          "p99_ms": 1000 * float(np.percentile(lat, 99)),
+                         "samples": int(lat.size),
                          "circuits_per_s": len(ids) / (last - first),
                          "c128_share": sum(1 for r in reqs if r.dtype == "c128") / len(reqs)})
+    return per_rate
+
+
+def run_serve(args):
+    """The serving workload at every rate of --rates, --requests arrivals each."""
+    import torch
+    from paper_2604_03816_gb300 import sv
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    with ClockSampler(None) as clk:
+        per_rate = serve_rates(sv, [float(r) for r in args.rates.split(",")], args.requests)
     best = max(per_rate, key=lambda d: d["circuits_per_s"])
     out = {"metric": "served circuits/s with p50/p99 latency (Poisson arrivals, 10-30 qubits, "
                      "70% c64 / 30% c128, top-64)",
@@ -488,8 +508,8 @@ def run_serve(args):
            "steps": len(per_rate), "warmup": 0, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "mixed f32/f64", "data": "synthetic",
            "config": {"workload": "serving_stream", "budget_gib": 150, "max_slots": 16,
-                      "max_k": 4, "max_requests_per_rate": args.max_requests},
-           "per_rate": per_rate}
+                      "max_k": 4, "requests_per_rate": args.requests},
+           "per_rate": per_rate, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
 
@@ -505,7 +525,7 @@ def config_dict(args, ngates, nfused):
             "seed": W.seed_for(3, args.n)}
 
 
-def run_batched(args):
+def run_batched(args, steps=None, warmup=None):
     """512 hardware-efficient-ansatz circuits (widths U{16,18,20,22}, 6 layers of
     RY RZ + CNOT ladder, complex64), <sum Z_i Z_{i+1}> per circuit.  Per width: one batch,
     fusion width and chunking from the autotuner (tuned once, before timing).  One step =
@@ -517,6 +537,8 @@ def run_batched(args):
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     fam = W.hea_batch(args.count)
     widths = sorted({w for w, _ in fam})
     groups = {w: [g for ww, g in fam if ww == w] for w in widths}
@@ -562,14 +584,14 @@ def run_batched(args):
                 out[w] = sv.sv_batch_expect(batches[w], xs, zs, cs)
             return fuse_s, out
 
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         fuse_total = 0.0
         with ClockSampler(None) as clk:
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 fs, out = step()
                 fuse_total += fs
             e1.record(stream)
@@ -593,20 +615,210 @@ def run_batched(args):
         torch.cuda.synchronize()
         unb = len(sample) / (f0.elapsed_time(f1) / 1000.0)
         s1.free()
-    value = args.count * args.steps / (ms / 1000.0)
+    value = args.count * steps / (ms / 1000.0)
     out = {"metric": "batched circuits/s (HEA, 16-22 qubits, complex64, <sum ZZ> per circuit)",
-           "value": value, "unit": "circuits/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "value": value, "unit": "circuits/s", "n_gpus": world, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"{args.count} hea circuits, widths {widths}, 6 layers, c64",
                       "per_width": {str(w): {"circuits": len(groups[w]),
                                              "best_k": tune[w]["best_k"],
                                              "l2_chunk_bytes": tune[w]["l2_bytes"],
                                              "tune_ms": tune[w]["ms"]} for w in widths}},
-           "host_fusion_s_per_step": fuse_total / args.steps,
+           "host_fusion_s_per_step": fuse_total / steps,
            "unbatched_circuits_per_s": unb,
            "speedup_vs_unbatched": value / unb, "clocks": clk.summary()}
+    for b in batches.values():
+        b.free()
+    for st in states.values():
+        st.free()
+    return out
+
+
+def time_config(sv, torch, n, dtype, k, circuits, warmup, cycles=24):
+    """One grid_random configuration on its own stream: `circuits` timed circuits after
+    `warmup` untimed ones, each sv_fuse (host) + sv_set_basis + sv_apply_circuit (adaptive
+    for complex64) + sv_topk(64).  The state is larger than L2 (no flush needed)."""
+    stream = torch.cuda.Stream()
+    specs = W.grid_random(n, cycles)
+    gates = sv.GateArray(sv.gates_from_specs(specs))
+    st = sv.sv_alloc(n, dtype, stream=stream)
+
+    def one(timing):
+        c = sv.sv_fuse(gates, n, k)
+        if sv.sv_info(st)[1] != dtype:
+            sv.sv_set_dtype(st, dtype)
+        sv.sv_set_basis(st, 0)
+        rep = sv.sv_apply_circuit(st, c, adaptive=(dtype == sv.SV_C64), timing=timing)
+        sv.sv_topk(st, 64)
+        return rep, len(c)
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            one(False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(None) as clk:
+            e0.record(stream)
+            runs = [one(True) for _ in range(circuits)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+    st.free()
+    ms = e0.elapsed_time(e1) / circuits
+    reps = [r for r, _ in runs]
+    apply_ms = sum(r["apply_ms"] for r in reps)
+    abytes = sum(r["bytes"] for r in reps)
+    achieved = abytes / (apply_ms / 1000.0) / 1e9
+    peak, peak_kind = hbm_peak()
+    return {"workload": f"grid_random {n}q depth {cycles}", "n_qubits": n,
+            "dtype": "c64" if dtype == sv.SV_C64 else "c128", "max_k": k,
+            "max_k_used": reps[-1]["max_k_used"], "gates": len(specs),
+            "fused_gates": runs[-1][1], "passes_per_circuit": reps[-1]["passes"],
+            "tensor_core_passes": reps[-1]["tc_passes"], "circuits": circuits,
+            "ms_per_circuit": ms, "circuits_per_s": 1000.0 / ms,
+            "apply_ms_per_circuit": apply_ms / circuits,
+            "fused_gate_hbm_gbs": achieved, "roofline_frac": achieved / peak,
+            "peak_gbs": peak, "peak_kind": peak_kind,
+            "promotions": sum(r["promotions"] for r in reps),
+            "state_bytes": (8 if dtype == sv.SV_C64 else 16) << n, "clocks": clk.summary()}
+
+
+def run_shard(args):
+    """One state over all ranks (global-qubit sharding): --n qubits per GPU, so n + g qubits
+    on 2^g ranks (weak scaling: the amplitudes per GPU are fixed).  One step = sv_fuse
+    (host) + the plan + every segment's passes and every exchange + the FP64 norm (one sum
+    over the ranks) + top-64.  Under torchrun every rank is one GPU and the exchanges are
+    NCCL send/recv; with --emulate-ranks R the R ranks are threads on one GPU and an
+    exchange is a device copy (a check of the path, not of NVLink)."""
+    import torch
+    from paper_2604_03816_gb300 import sv
+    from paper_2604_03816_gb300.shard import (GpuShard, ShardedState, ThreadComm, ThreadHub,
+                                              TorchComm)
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dt = sv.SV_C64 if args.dtype == "c64" else sv.SV_C128
+    emulate = args.emulate_ranks if world == 1 else 0
+    ranks = emulate if emulate else world
+    g = ranks.bit_length() - 1
+    if (1 << g) != ranks:
+        raise SystemExit("shard: the number of ranks must be a power of two")
+    n_total = args.n if emulate else args.n + g
+    specs = W.grid_random(n_total, args.cycles)
+    gates = sv.GateArray(sv.gates_from_specs(specs))
+
+    def run_rank(r, comm, result):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            shard = GpuShard(n_total - g, dt, stream=stream)
+            st = ShardedState(n_total, dt, comm, shard)
+
+            def step():
+                c = sv.sv_fuse(gates, n_total, args.k)
+                st.set_basis(0)
+                rep = st.apply_circuit(c)
+                return rep, st.norm(), st.topk(64)
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            comm.sum(0.0)                                   # all ranks start together
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bytes0 = st.exchanged_bytes
+            for _ in range(args.steps):
+                rep, norm, top = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            result[r] = {"ms": comm.allgather(ms), "rep": rep, "norm": norm,
+                         "exchanged_bytes_per_step": (st.exchanged_bytes - bytes0) / args.steps}
+            shard.free()
+
+    result = {}
+    with ClockSampler(None) as clk:
+        if emulate:
+            import threading
+            hub = ThreadHub(ranks)
+            errs = []
+
+            def worker(r):
+                try:
+                    torch.cuda.set_device(local)
+                    run_rank(r, ThreadComm(hub, r), result)
+                except BaseException as e:     # noqa: BLE001
+                    errs.append(e)
+                    hub.barrier.abort()
+            th = [threading.Thread(target=worker, args=(r,)) for r in range(ranks)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+            if errs:
+                raise errs[0]
+            me = result[0]
+        else:
+            import torch.distributed as dist
+            if world > 1:
+                dist.init_process_group("nccl")
+                run_rank(rank, TorchComm(), result)
+                me = result[rank]
+            else:
+                class _One:
+                    rank, world = 0, 1
+
+                    def sum(self, v):
+                        return v
+
+                    def allgather(self, o):
+                        return [o]
+                run_rank(0, _One(), result)
+                me = result[0]
+    ms = max(me["ms"])
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    value = args.steps / (ms / 1000.0)
+    out = {"metric": "sharded circuits/s (one state over the ranks, global-qubit sharding)",
+           "value": value, "unit": "circuits/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if dt == sv.SV_C64 else "f64", "data": "synthetic",
+           "config": {"workload": f"grid_random {n_total}q depth {args.cycles}, {args.dtype}, "
+                                  f"fusion k={args.k}, {ranks} ranks x 2^{n_total - g} amplitudes"
+                                  + (" (threads on one GPU, exchanges as device copies)" if emulate
+                                     else " (one GPU each, NCCL exchanges)"),
+                      "ranks": ranks, "local_qubits": n_total - g},
+           "passes_per_step": me["rep"]["passes"], "exchanges_per_step": me["rep"]["exchanges"],
+           "swap_passes_per_step": me["rep"]["swap_passes"],
+           "exchanged_bytes_per_step_per_rank": me["exchanged_bytes_per_step"],
+           "norm": me["norm"], "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
+
+
+def run_extras(args, sv, torch):
+    """The rest of the headline metric, measured in the default run after the 30-qubit
+    line: the grid circuits at 28 and 33 qubits (complex64) and at 30 and 32 qubits
+    (complex128, the width-5 schedule too), short batched and served summaries."""
+    out = {}
+    cfgs = [(28, sv.SV_C64, 5, 8, 2), (33, sv.SV_C64, 5, 3, 1), (30, sv.SV_C128, 4, 3, 1),
+            (30, sv.SV_C128, 5, 2, 1), (32, sv.SV_C128, 4, 2, 1)]
+    out["configs"] = [time_config(sv, torch, n, dt, k, nc, nw) for n, dt, k, nc, nw in cfgs]
+    torch.cuda.empty_cache()
+    b = run_batched(args, steps=3, warmup=2)
+    out["batched"] = {kk: b[kk] for kk in ("metric", "value", "unit", "ms_per_step", "steps",
+                                           "warmup", "speedup_vs_unbatched",
+                                           "unbatched_circuits_per_s", "clocks")}
+    out["batched"]["per_width"] = b["config"]["per_width"]
+    torch.cuda.empty_cache()
+    with ClockSampler(None) as clk:
+        per_rate = serve_rates(sv, [10.0, 100.0], 100)
+    out["serving"] = {"workload": "serving_stream: Poisson arrivals, width U{10..30}, depth "
+                                  "U{10..60}, 70% c64 / 30% c128, top-64, 150 GiB budget, 16 slots, "
+                                  "fusion k = 4; 100 arrivals per rate (bench.py --mode serve "
+                                  "runs 500 per rate over six rates)",
+                      "per_rate": per_rate, "clocks": clk.summary()}
+    return out
 
 
 def main():
@@ -615,7 +827,7 @@ def main():
         run_reference(args)
         return
     if args.mode == "batched":
-        run_batched(args)
+        print(json.dumps(run_batched(args)), flush=True)
         return
     if args.mode == "serve":
         run_serve(args)
@@ -628,6 +840,9 @@ def main():
         return
     if args.mode == "qft":
         run_qft(args)
+        return
+    if args.mode == "shard":
+        run_shard(args)
         return
     rank, world, local = dist_info()
     import torch
@@ -767,7 +982,7 @@ def main():
             del h_in, h_outs
 
         unfused = None
-        if args.compare_unfused:
+        if not args.no_compare_unfused and world == 1:
             s128 = sv.sv_alloc(args.n, sv.SV_C128, stream=stream)
             cu = sv.sv_fuse(gates, args.n, 0)
             r = sv.sv_apply_circuit(s128, cu, timing=True)
@@ -778,6 +993,9 @@ def main():
 
     fuser.shutdown(wait=True)
     state.free()
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = run_extras(args, sv, torch)
     if rank != 0:
         return
     value = job_throughput(world, args.steps, ms)
@@ -804,6 +1022,8 @@ def main():
     if unfused:
         out["unfused_c128"] = unfused
         out["speedup_vs_unfused_c128"] = value / unfused["circuits_per_s"]
+    if extras:
+        out.update(extras)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

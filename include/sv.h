@@ -89,8 +89,9 @@ sv_status sv_gate_matrix(uint32_t kind, const double *params, uint32_t nparams, 
 
 /* --------------------------------------------------------------------- states */
 
-/* Create an n-qubit state (1 <= n <= SV_MAX_QUBITS) in dtype on the current CUDA
- * device, initialised to |0...0>.
+/* The backend's initialisation operation (Section 4.1): create an n-qubit state
+ * (1 <= n <= SV_MAX_QUBITS) in dtype on the current CUDA device, holding the 2^n
+ * amplitudes of Eq. 1, initialised to |0...0>.
  *   dev_buf: caller-owned device buffer of `bytes` bytes (16-byte aligned, at least
  *            2^n * 8 (C64) or 2^n * 16 (C128) bytes), or NULL for a library-owned
  *            buffer of exactly the state's size.  A caller buffer must outlive the state.
@@ -112,8 +113,9 @@ sv_status sv_set_dtype(sv_state *s, sv_dtype dtype);
 /* Copy 2^n amplitudes in the state's dtype from src (host or device memory).  Host
  * sources are copied synchronously; pinned host memory is fastest. */
 sv_status sv_set_state(sv_state *s, const void *src, int src_on_device);
-/* Copy the 2^n amplitudes (state's dtype, logical qubit order) to dst.  To host:
- * synchronises.  To device: asynchronous. */
+/* Read out |psi> = sum_k alpha_k |k> (Eq. 1): copy the 2^n amplitudes (state's dtype,
+ * index order, qubit t = bit t) to dst.  To host: synchronises.  To device:
+ * asynchronous. */
 sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device);
 
 /* ------------------------------------------------------------------ fusion (F) */
@@ -179,16 +181,36 @@ typedef struct {
     uint64_t bytes;             /* algorithmic HBM bytes of the passes: 2 * 2^n * s per dense
                                    pass, 2 * s per touched amplitude of a structured one */
     double apply_ms;            /* with opts->timing: CUDA-event time of all passes (ms) */
+    uint64_t tc_passes;         /* passes that ran on the tensor-core kernels */
+    uint32_t max_k_used;        /* widest gate of the schedule that produced the final state */
 } sv_apply_report;
 
-/* Apply every gate of the fused schedule, in order, one pass over the state each.
- * opts may be NULL (no adaptivity).  With opts->adaptive and a C64 state, the FP64 norm
- * is measured before and after (and every drift_check_every passes); if the drift
- * exceeds drift_threshold the state is re-initialised in complex128 from its value at
- * the start of the call and the whole schedule is replayed in complex128 (Section 5.4
- * made runtime).  Promotion needs a buffer of 2^n * 16 bytes: a library-owned buffer is
- * reallocated, a caller buffer must already be that large (else SV_ERR_STATE).  report
- * may be NULL.  Asynchronous unless adaptive. */
+/* Apply every gate of the fused schedule, in order, one pass over the state each (Eq. 10:
+ * the fused product equals the unfused one).  opts may be NULL (no adaptivity).
+ *
+ * Precision (Section 5.4).  complex64 states compute in FP32 (tensor-core passes on exact
+ * 9-bit fixed-point slices with FP32-level error relative to each group's largest
+ * amplitude).  complex128 states compute to FP64 accuracy: the CUDA-core kernels in FP64
+ * FMA; the complex128 tensor-core kernel (gates of up to 4 qubits) in block fixed point,
+ * each group of amplitudes on the grid of its largest exponent, with an absolute error
+ * per output of at most 2^-46 x (the group's largest amplitude) x (the gate's largest
+ * entry) plus half an ulp -- components far below their group's largest keep that
+ * absolute accuracy, not FP64's relative one.  A complex128 state runs a circuit that
+ * has width-5 gates as the same input gates fused at width 4 (built once per circuit),
+ * so that every dense pass stays on the tensor cores (report->max_k_used says which).
+ *
+ * With opts->adaptive and a C64 state, the FP64 norm is measured before and after (and
+ * every drift_check_every passes); if the drift exceeds drift_threshold the state is
+ * re-initialised in complex128 from its value at the start of the call and the whole
+ * circuit is replayed in complex128 (Section 5.4 made runtime).  A start state that is
+ * not a basis state (sv_set_state, or earlier gates) is kept in a complex64 snapshot of
+ * 2^n * 8 bytes, allocated on first need and kept by the state until sv_free.
+ * Promotion needs a buffer of 2^n * 16 bytes: a library-owned buffer is reallocated (the
+ * new one before the old one is released; if memory is short the old one is released
+ * first, and if even that fails the call returns SV_ERR_OOM and the state has no buffer:
+ * every call but sv_set_dtype, sv_info and sv_free then returns SV_ERR_STATE); a caller
+ * buffer must already be that large (else SV_ERR_STATE).  report may be NULL.
+ * Asynchronous unless adaptive. */
 sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts *opts,
                            sv_apply_report *report);
 
@@ -199,7 +221,9 @@ sv_status sv_apply_gate(sv_state *s, const sv_gate *g);
 
 /* sum_k |alpha_k|^2 accumulated in FP64 (Eq. 1).  Synchronises. */
 sv_status sv_norm(sv_state *s, double *out);
-/* p_k = |alpha_k|^2 for all 2^n outcomes in index order: float (C64) or double (C128).
+/* The Z-basis measurement distribution of Eq. 1 (the backend's measurement operation,
+ * Section 4.1): p_k = |alpha_k|^2 for all 2^n outcomes in index order: float (C64) or
+ * double (C128).
  * out_on_device: out is device memory (asynchronous) or host memory (synchronises).  Host
  * memory that is page-locked and mapped for the device (cudaHostAlloc, torch pin_memory)
  * is written by the kernel directly; other host memory goes through a device temporary of
@@ -235,8 +259,10 @@ sv_status sv_density_probs(sv_state *s, void *out, int out_on_device);
  * 2^n / 4 bytes (plus 8 bytes per shot for host output), kept by the state for the next
  * call and released by sv_free.  SV_ERR_STATE if T = 0 (a zero state).  Synchronises. */
 sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64_t *out, int out_on_device);
-/* The min(k, 2^n) most probable outcomes (1 <= k <= 64), sorted by probability
- * descending, ties to the lower index.  idx/p are host arrays of k entries.  Synchronises. */
+/* The min(k, 2^n) most probable outcomes of the Z-basis distribution p_k = |alpha_k|^2
+ * (Eq. 1; the backend's measurement operation of Section 4.1 reduced to its head),
+ * sorted by probability descending, ties to the lower index.  idx/p are host arrays of
+ * k entries.  Synchronises. */
 sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
 
 /* ------------------------------------------------------ structure-aware application */
@@ -352,7 +378,9 @@ typedef struct {
     size_t budget_bytes;     /* HBM budget of admitted requests (0: 150 GiB) */
     uint32_t max_slots;      /* requests in flight on the GPU (0: 16; at most 256) */
     uint32_t topk;           /* outcomes per result, 1..64 (0: 64) */
-    uint32_t max_k;          /* fusion width 1..5 (0: 4) */
+    uint32_t max_k;          /* fusion width 1..5 (0: 4); complex128 requests of 11 or more
+                                qubits are fused at min(max_k, 4), the widest gate of the
+                                complex128 tensor-core pass */
     uint32_t fuse_threads;   /* host threads that fuse submitted circuits (0: 4) */
 } sv_server_config;
 
@@ -390,10 +418,13 @@ sv_status sv_server_destroy(sv_server *s);
 /* sum_t coef[t] <psi| P_t |psi> (as sv_expect) for a caller-owned device state, written
  * to out_dev (one double in device memory), enqueued on `stream` (NULL = the legacy
  * default stream) -- without allocating anything.  No counterpart in the paper: it
- * exists for callers that cannot call cudaMalloc or cudaFree, such as code running
- * inside a global-mode CUDA stream capture, a host framework that owns the whole
- * device-memory budget, or a latency-critical loop that must not synchronise the device.
- *   psi: 2^n amplitudes in dtype, 16-byte aligned device memory; n in 1..34.
+ * exists for callers that cannot call cudaMalloc or cudaFree, such as a host framework
+ * that owns the whole device-memory budget through its own pool, or a latency-critical
+ * loop where an allocation would synchronise the device and stall other streams.
+ *   psi: 2^n amplitudes in dtype, 16-byte aligned device memory of the current device;
+ *        n in 1..34.
+ *   out_dev: 8-byte aligned device memory of the current device.  A host pointer or
+ *        another device's memory for either is rejected with SV_ERR_ARG.
  * Scratch: a fixed 128 KiB device array inside the library (one FP64 partial per block
  * for each batch of up to 32 terms sharing an X-part; at most 64 batches, else
  * SV_ERR_ARG).  Every GPU that loads the library holds it until the process exits.  The
@@ -405,6 +436,61 @@ sv_status sv_server_destroy(sv_server *s);
 sv_status sv_expect_noalloc(const void *psi, uint32_t n, sv_dtype dtype, const uint64_t *xmask,
                             const uint64_t *zmask, const double *coef, size_t nterms,
                             double *out_dev, void *stream);
+
+/* --------------------------------------------------- global-qubit sharding (2^g GPUs) */
+
+/* The paper keeps the state on one device and names device memory as the design's
+ * ceiling (Section 10) and multi-device partitioning as future work (Section 11).  A
+ * sharded state splits the 2^n amplitudes by their top g index bits over 2^g processes:
+ * rank r holds, as an ordinary state of L = n - g qubits (sv_alloc(L, ...)), the
+ * amplitudes r 2^L .. (r + 1) 2^L - 1 in index order.  A plan turns a fused circuit into
+ * steps that every rank runs in the same order:
+ *   SV_SHARD_APPLY: sv_apply_circuit(shard, segment) -- the gates whose targets are all
+ *     local, relabelled to the bit positions their qubits occupy at that point;
+ *   SV_SHARD_SWAP (local_bit p, global_bit j): an exchange with the partner rank
+ *     r ^ 2^j.  With b = bit j of r, each rank sends the 2^(L-1) amplitudes whose local
+ *     index bit p is 1 - b (in index order, e.g. via sv_shard_pack) and puts the
+ *     partner's 2^(L-1) amplitudes into the same places (sv_shard_unpack); the qubit at
+ *     position p and the one at global position j trade places.
+ * Swaps are chosen before each gate that touches a qubit at a global position: the local
+ * position whose qubit is used again latest is given up (ties: the highest position,
+ * whose half is contiguous).  At the end every qubit is moved back to its own position
+ * (exchanges, then SWAP passes inside the shards), so the shards again hold the amplitudes
+ * in index order; a norm or a Pauli expectation without X/Y on the top g qubits is then
+ * the sum over ranks of the shard's value, with the coefficient's sign from the Z part on
+ * the top qubits, (-1)^popcount(zmask >> L & r).  complex128 plans use the circuit's
+ * width-4 schedule when it has width-5 gates.  Host only; the transport (NCCL, or a copy
+ * between processes) is the caller's. */
+#define SV_SHARD_APPLY 0u
+#define SV_SHARD_SWAP 1u
+typedef struct sv_shard_plan sv_shard_plan;
+/* g in 0..16, g < n; SV_ERR_ARG if L = n - g is smaller than the widest gate (or 2). */
+sv_status sv_shard_plan_create(const sv_circuit *c, uint32_t g, sv_dtype dtype, sv_shard_plan **out);
+sv_status sv_shard_plan_free(sv_shard_plan *p);
+/* Steps, exchanges and SWAP passes of the plan. */
+sv_status sv_shard_plan_info(const sv_shard_plan *p, size_t *nsteps, uint64_t *exchanges,
+                             uint64_t *local_swaps);
+/* Step i: its kind, the swap's positions (SV_SHARD_SWAP) or the segment (SV_SHARD_APPLY; a
+ * circuit on L qubits owned by the plan, valid until sv_shard_plan_free). */
+sv_status sv_shard_plan_step(const sv_shard_plan *p, size_t i, uint32_t *kind, uint32_t *local_bit,
+                             uint32_t *global_bit, const sv_circuit **segment);
+/* Copy elements offset .. offset + count - 1 of the half of the state whose index bit `bit`
+ * is `value` (2^(n-1) amplitudes in index order) to the device buffer dst_dev (pack), or
+ * from src_dev back into those places (unpack).  Buffers hold count amplitudes of the
+ * state's dtype, 16-byte aligned for complex128 (8-byte for complex64).  Asynchronous on
+ * the state's stream; HBM-bound copies. */
+sv_status sv_shard_pack(sv_state *s, uint32_t bit, uint32_t value, uint64_t offset, uint64_t count,
+                        void *dst_dev);
+sv_status sv_shard_unpack(sv_state *s, uint32_t bit, uint32_t value, uint64_t offset, uint64_t count,
+                          const void *src_dev);
+/* All amplitudes zero (a shard that holds none of |x>).  Asynchronous. */
+sv_status sv_set_zero(sv_state *s);
+
+/* Testing aid (no counterpart in the paper): the next `count` allocations of a state
+ * buffer (sv_alloc, sv_set_dtype, a promotion) fail as if device memory were exhausted,
+ * so that tests can drive the out-of-memory paths without exhausting the GPU.  0 turns
+ * it off.  Host only; process-wide. */
+sv_status sv_debug_fail_allocs(uint32_t count);
 
 sv_status sv_sync(sv_state *s);   /* wait for the state's stream; reports device errors */
 const char *sv_last_error(void);  /* thread-local, never NULL */

@@ -12,7 +12,7 @@ Follows Section 5 of the paper in its own order:
   The fused gate replaces u with U_fused = U_v . U_u on q(u) | q(v); v's edges move to
   u and v is removed.  The sweep then moves on to the next vertex.
 
-Readings where the paper is silent or ambiguous (each one is listed in the design doc):
+Readings where the paper is silent or ambiguous:
 
 * Condition (3) is read as "contracting the edge (u, v) keeps the graph acyclic": there
   is no other directed path from u to v.  This implies the printed condition (no other

@@ -180,16 +180,21 @@ sv_status launch_apply_t(sv_state *s, const svi::Gate &g) {
 
 namespace svi {
 
-sv_status launch_apply(sv_state *s, const Gate &g, uint64_t *bytes) {
+sv_status launch_apply(sv_state *s, const Gate &g, uint64_t *bytes, int *kind) {
     if (g.k < 1 || g.k > SV_MAX_K || g.k > s->n)
         return set_error(SV_ERR_ARG, "apply: gate width out of range");
     if (!(s->policy & SV_POLICY_DENSE_ONLY)) {
         const Structure st = classify(g);
-        if (struct_preferred(s, st)) return launch_apply_struct(s, st, bytes);
+        if (struct_preferred(s, st)) {
+            if (kind) *kind = PASS_STRUCTURED;
+            return launch_apply_struct(s, st, bytes);
+        }
     }
     if (bytes) *bytes = 2ull * ((s->dtype == SV_C64 ? 8ull : 16ull) << s->n);
+    if (kind) *kind = PASS_TENSOR_CORE;
     if (tc_eligible(s, g)) return launch_apply_tc(s, g);
     if (tc64_eligible(s, g)) return launch_apply_tc64(s, g);
+    if (kind) *kind = PASS_CUDA_CORE;
     if (s->dtype == SV_C64) {
         switch (g.k) {
             case 1: return svk::launch_apply_t<float, 1>(s, g);

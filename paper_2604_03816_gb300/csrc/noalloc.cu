@@ -1,12 +1,11 @@
 // sv_expect_noalloc: the Pauli-expectation reduction with no memory allocation at all.
 //
-// Who needs it: code that must not call cudaMalloc or cudaFree -- a caller in the
-// middle of a global-mode CUDA stream capture (where cudaMalloc is not permitted),
-// a host framework that owns the whole device-memory budget through its own pool and
-// forbids side allocations, or a latency-critical loop where an allocation would
-// synchronise the device and stall other streams.  Such a caller cannot create an
-// sv_state (sv_alloc allocates a workspace), so this entry point works on a raw device
-// state vector that the caller owns.
+// Who needs it: code that must not call cudaMalloc or cudaFree -- a host framework that
+// owns the whole device-memory budget through its own pool and forbids side
+// allocations, or a latency-critical loop where an allocation would synchronise the
+// device and stall the other streams.  Such a caller cannot create an sv_state
+// (sv_alloc allocates a workspace), so this entry point works on a raw device state
+// vector that the caller owns.
 //
 // The kernel's scratch memory (one FP64 partial sum per block per batch of terms) lives
 // in a file-scope __device__ array of fixed size, which every GPU that loads the library
@@ -64,6 +63,28 @@ extern "C" sv_status sv_expect_noalloc(const void *psi, uint32_t n, sv_dtype dty
         return svi::set_error(SV_ERR_ARG, "sv_expect_noalloc: bad dtype");
     if (reinterpret_cast<uintptr_t>(psi) & 15u)
         return svi::set_error(SV_ERR_ARG, "sv_expect_noalloc: state must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out_dev) & 7u)
+        return svi::set_error(SV_ERR_ARG, "sv_expect_noalloc: out_dev must be 8-byte aligned");
+    // Both pointers must be device (or managed) memory that the current device can use: a
+    // host pointer or another device's memory would reach the kernel and fault.
+    int dev = 0;
+    SV_CUDA(cudaGetDevice(&dev));
+    const void *ptrs[2] = {psi, out_dev};
+    const char *names[2] = {"psi", "out_dev"};
+    for (int i = 0; i < 2; ++i) {
+        cudaPointerAttributes pa;
+        const cudaError_t e = cudaPointerGetAttributes(&pa, ptrs[i]);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return svi::set_error(SV_ERR_ARG, std::string("sv_expect_noalloc: ") + names[i] +
+                                                  " is not a CUDA pointer (" + cudaGetErrorString(e) + ")");
+        }
+        const bool on_dev = (pa.type == cudaMemoryTypeDevice && pa.device == dev) ||
+                            pa.type == cudaMemoryTypeManaged;
+        if (!on_dev)
+            return svi::set_error(SV_ERR_ARG, std::string("sv_expect_noalloc: ") + names[i] +
+                                                  " must be device memory of the current device");
+    }
     const uint64_t lim = (1ull << n) - 1;
     for (size_t t = 0; t < nterms; ++t)
         if ((xmask[t] & ~lim) || (zmask[t] & ~lim))

@@ -221,6 +221,7 @@ extern "C" sv_status sv_sample(sv_state *s, uint64_t seed, size_t nshots, uint64
                                int out_on_device) {
     clear_error();
     if (!s || !out) return set_error(SV_ERR_ARG, "sv_sample: null argument");
+    if (check_live(s, "sv_sample") != SV_OK) return SV_ERR_STATE;
     if (nshots == 0) return SV_OK;
     const unsigned long long N = 1ull << s->n;
     const uint32_t B = (uint32_t)std::min<unsigned long long>(64, N);

@@ -101,7 +101,11 @@ void fuser_loop(sv_server *S) {
             r->fuse_status = SV_ERR_OOM;
         } else {
             c->n = r->n;
-            c->gates = svi::fuse_gates(r->gates, r->n, S->cfg.max_k);
+            // complex128 width-5 gates have no tensor-core pass: such requests are fused at
+            // width <= 4 where the complex128 tensor-core kernel serves the state
+            const uint32_t kf = (r->dtype == SV_C128 && r->n >= 11) ? std::min(S->cfg.max_k, 4u)
+                                                                    : S->cfg.max_k;
+            c->gates = svi::fuse_gates(r->gates, r->n, kf);
             r->gates.clear();
             r->gates.shrink_to_fit();
             r->circuit = c;

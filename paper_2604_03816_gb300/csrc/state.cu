@@ -3,6 +3,7 @@
 // apply_kernels.cu and reduce_kernels.cu.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -51,6 +52,65 @@ static sv_status validate_gate(const sv_gate *g, uint32_t n, const char *who) {
     return SV_OK;
 }
 
+// Test hook: the next g_fail_allocs state-buffer allocations fail (sv_debug_fail_allocs).
+static std::atomic<uint32_t> g_fail_allocs{0};
+
+static cudaError_t alloc_state_buffer(void **p, size_t bytes) {
+    uint32_t left = g_fail_allocs.load();
+    while (left > 0 && !g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+    }
+    if (left > 0) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+// Give a library-owned state a buffer of `need` bytes.  The new buffer is allocated
+// before the old one is released, so a failure leaves the state as it was; only if that
+// fails is the old buffer released first and the allocation tried again.  If the second
+// try fails too, the state has no buffer (buf == nullptr): every call but sv_set_dtype,
+// sv_info and sv_free then returns SV_ERR_STATE instead of launching on it.
+static sv_status replace_buffer(sv_state *s, size_t need, const char *who) {
+    void *nb = nullptr;
+    SV_CUDA(cudaStreamSynchronize(s->stream));
+    cudaError_t e = alloc_state_buffer(&nb, need);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (s->buf) cudaFree(s->buf);
+        s->buf = nullptr;
+        s->cap = 0;
+        e = alloc_state_buffer(&nb, need);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return set_error(SV_ERR_OOM, std::string(who) + ": no device memory for a state buffer of " +
+                                             std::to_string(need) + " bytes; the state has no buffer "
+                                             "now (sv_set_dtype allocates one again)");
+        }
+    } else if (s->buf) {
+        SV_CUDA(cudaFree(s->buf));
+    }
+    s->buf = nb;
+    s->cap = need;
+    return SV_OK;
+}
+
+const std::vector<Gate> &narrow_schedule(const sv_circuit *c) {
+    bool wide = false;
+    for (const Gate &g : c->gates) wide = wide || g.k == 5;
+    if (!wide || c->in_gates.empty()) return c->gates;
+    std::call_once(c->narrow_once, [&] {
+        c->narrow = fuse_gates(c->in_gates, c->n, std::min(c->max_k, 4u), nullptr,
+                               (c->flags & SV_FUSE_COMMUTE) != 0);
+    });
+    return c->narrow;
+}
+
+// SV_ERR_STATE for a state left without a buffer by a failed reallocation.
+sv_status check_live(const sv_state *s, const char *who) {
+    if (!s->buf)
+        return set_error(SV_ERR_STATE, std::string(who) + ": the state has no buffer (a reallocation "
+                                                          "failed); call sv_set_dtype or sv_free");
+    return SV_OK;
+}
+
 static sv_status measure_norm(sv_state *s, double *out) {
     double *res = reinterpret_cast<double *>(s->ws + WS_RESULT) + 63;
     sv_status st = launch_norm(s, res);
@@ -96,8 +156,9 @@ sv_status sv_alloc(uint32_t n, sv_dtype dtype, void *dev_buf, size_t bytes, void
         s->cap = bytes;
         s->owned = false;
     } else {
-        e = cudaMalloc(&s->buf, need);
+        e = alloc_state_buffer(&s->buf, need);
         if (e != cudaSuccess) {
+            (void)cudaGetLastError();
             delete s;
             return set_error(SV_ERR_OOM, std::string("sv_alloc: state: ") + cudaGetErrorString(e));
         }
@@ -145,6 +206,7 @@ sv_status sv_info(const sv_state *s, uint32_t *n, sv_dtype *dtype, void **dev_pt
 sv_status sv_set_basis(sv_state *s, uint64_t x) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_set_basis: null state");
+    if (check_live(s, "sv_set_basis") != SV_OK) return SV_ERR_STATE;
     if (x >> s->n) return set_error(SV_ERR_ARG, "sv_set_basis: x >= 2^n");
     SV_CUDA(cudaMemsetAsync(s->buf, 0, state_bytes(s), s->stream));
     sv_status st = launch_set_one(s, x);
@@ -154,20 +216,25 @@ sv_status sv_set_basis(sv_state *s, uint64_t x) {
     return SV_OK;
 }
 
+sv_status sv_set_zero(sv_state *s) {
+    clear_error();
+    if (!s) return set_error(SV_ERR_ARG, "sv_set_zero: null state");
+    if (check_live(s, "sv_set_zero") != SV_OK) return SV_ERR_STATE;
+    SV_CUDA(cudaMemsetAsync(s->buf, 0, state_bytes(s), s->stream));
+    s->basis_known = false;
+    return SV_OK;
+}
+
 sv_status sv_set_dtype(sv_state *s, sv_dtype dtype) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_set_dtype: null state");
     if (dtype != SV_C64 && dtype != SV_C128) return set_error(SV_ERR_ARG, "sv_set_dtype: bad dtype");
     const size_t need = elem_bytes(dtype) << s->n;
-    if (s->cap < need) {
+    if (s->cap < need || !s->buf) {
         if (!s->owned)
             return set_error(SV_ERR_STATE, "sv_set_dtype: caller buffer too small for this dtype");
-        SV_CUDA(cudaStreamSynchronize(s->stream));
-        SV_CUDA(cudaFree(s->buf));
-        s->buf = nullptr;
-        s->cap = 0;
-        SV_CUDA(cudaMalloc(&s->buf, need));
-        s->cap = need;
+        const sv_status st = replace_buffer(s, need, "sv_set_dtype");
+        if (st != SV_OK) return st;
     }
     s->dtype = dtype;
     return sv_set_basis(s, 0);
@@ -176,6 +243,7 @@ sv_status sv_set_dtype(sv_state *s, sv_dtype dtype) {
 sv_status sv_set_state(sv_state *s, const void *src, int src_on_device) {
     clear_error();
     if (!s || !src) return set_error(SV_ERR_ARG, "sv_set_state: null argument");
+    if (check_live(s, "sv_set_state") != SV_OK) return SV_ERR_STATE;
     SV_CUDA(cudaMemcpyAsync(s->buf, src, state_bytes(s),
                             src_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                             s->stream));
@@ -187,6 +255,7 @@ sv_status sv_set_state(sv_state *s, const void *src, int src_on_device) {
 sv_status sv_get_state(sv_state *s, void *dst, int dst_on_device) {
     clear_error();
     if (!s || !dst) return set_error(SV_ERR_ARG, "sv_get_state: null argument");
+    if (check_live(s, "sv_get_state") != SV_OK) return SV_ERR_STATE;
     SV_CUDA(cudaMemcpyAsync(dst, s->buf, state_bytes(s),
                             dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             s->stream));
@@ -211,6 +280,7 @@ static sv_status make_circuit(const std::vector<Gate> &in, uint32_t n, uint32_t 
             if (flags & SV_FUSE_COMMUTE) c->in_diag.push_back(diagonal_mask(g));
         }
         c->gates = fuse_gates(in, n, max_k, &c->plan, (flags & SV_FUSE_COMMUTE) != 0);
+        c->in_gates = in;
     } catch (const std::bad_alloc &) {
         delete c;
         return set_error(SV_ERR_OOM, std::string(who) + ": host allocation failed");
@@ -326,6 +396,7 @@ sv_status sv_fuse_like(const sv_circuit *pattern, const sv_gate *gates, size_t n
         c->in_t = pattern->in_t;
         c->in_diag = pattern->in_diag;
         c->plan = pattern->plan;
+        c->in_gates = in;
         c->gates = replay_fusion(std::move(in), pattern->plan);
     } catch (const std::bad_alloc &) {
         delete c;
@@ -390,6 +461,7 @@ sv_status sv_gate_structure(const sv_gate *g, uint32_t *kind, uint32_t *control_
 sv_status sv_apply_gate(sv_state *s, const sv_gate *g) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_apply_gate: null state");
+    if (check_live(s, "sv_apply_gate") != SV_OK) return SV_ERR_STATE;
     sv_status st = validate_gate(g, s->n, "sv_apply_gate");
     if (st != SV_OK) return st;
     s->basis_known = false;
@@ -398,7 +470,7 @@ sv_status sv_apply_gate(sv_state *s, const sv_gate *g) {
 
 // Enqueue passes [begin, end).  With `timing`, CUDA events on the state's stream bracket
 // the passes and their elapsed time is added to *ms (this synchronises on the events).
-static sv_status run_schedule(sv_state *s, const sv_circuit *c, size_t begin, size_t end,
+static sv_status run_schedule(sv_state *s, const std::vector<Gate> &gates, size_t begin, size_t end,
                               bool timing, sv_apply_report *r) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timing) {
@@ -409,8 +481,11 @@ static sv_status run_schedule(sv_state *s, const sv_circuit *c, size_t begin, si
     sv_status st = SV_OK;
     for (size_t i = begin; i < end && st == SV_OK; ++i) {
         uint64_t b = 0;
-        st = launch_apply(s, c->gates[i], &b);
+        int kind = PASS_CUDA_CORE;
+        st = launch_apply(s, gates[i], &b, &kind);
         r->bytes += b;
+        if (kind == PASS_TENSOR_CORE) ++r->tc_passes;
+        r->max_k_used = std::max(r->max_k_used, gates[i].k);
     }
     r->passes += end - begin;
     if (timing) {
@@ -427,10 +502,22 @@ static sv_status run_schedule(sv_state *s, const sv_circuit *c, size_t begin, si
     return st;
 }
 
+// The schedule a state of this dtype runs.  The complex128 tensor-core kernel takes gates
+// of up to four qubits; width-5 gates would run on the FP64 CUDA cores at a small
+// fraction of its rate, so complex128 states run the circuit's input gates fused again
+// at width <= 4 (same flags; Algorithm 2 is deterministic, so this schedule is fixed by
+// the circuit and built once).
+static const std::vector<Gate> &schedule_for(const sv_state *s, const sv_circuit *c) {
+    if (s->dtype != SV_C128 || (s->policy & SV_POLICY_NO_TENSOR_CORES) || !tc64_eligible(s, Gate()))
+        return c->gates;
+    return narrow_schedule(c);
+}
+
 sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts *opts,
                            sv_apply_report *rep) {
     clear_error();
     if (!s || !c) return set_error(SV_ERR_ARG, "sv_apply_circuit: null argument");
+    if (check_live(s, "sv_apply_circuit") != SV_OK) return SV_ERR_STATE;
     if (c->n != s->n) return set_error(SV_ERR_ARG, "sv_apply_circuit: circuit built for another n");
     for (const Gate &g : c->gates)
         if (g.k > s->n) return set_error(SV_ERR_ARG, "sv_apply_circuit: gate wider than the state");
@@ -442,7 +529,7 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts
     const bool timing = opts && opts->timing;
     if (!adaptive) {
         s->basis_known = false;
-        sv_status st = run_schedule(s, c, 0, G, timing, &r);
+        sv_status st = run_schedule(s, schedule_for(s, c), 0, schedule_for(s, c).size(), timing, &r);
         if (st != SV_OK) return st;
         if (rep) *rep = r;
         return SV_OK;
@@ -470,7 +557,7 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts
     size_t done = 0;
     while (done < G && !promote) {
         const size_t next = every ? std::min(G, done + every) : G;
-        st = run_schedule(s, c, done, next, timing, &r);
+        st = run_schedule(s, c->gates, done, next, timing, &r);
         if (st != SV_OK) return st;
         done = next;
         st = measure_norm(s, &r.norm_after);
@@ -485,12 +572,8 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts
             if (!s->owned)
                 return set_error(SV_ERR_STATE, "sv_apply_circuit: promotion to complex128 needs a "
                                                "caller buffer of 2^n * 16 bytes");
-            SV_CUDA(cudaStreamSynchronize(s->stream));
-            SV_CUDA(cudaFree(s->buf));
-            s->buf = nullptr;
-            s->cap = 0;
-            SV_CUDA(cudaMalloc(&s->buf, bytes128));
-            s->cap = bytes128;
+            st = replace_buffer(s, bytes128, "sv_apply_circuit (promotion to complex128)");
+            if (st != SV_OK) return st;
         }
         s->dtype = SV_C128;
         if (from_basis) {
@@ -500,7 +583,9 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts
         }
         if (st != SV_OK) return st;
         s->basis_known = false;
-        st = run_schedule(s, c, 0, G, timing, &r);
+        r.max_k_used = 0;
+        const std::vector<Gate> &replay = schedule_for(s, c);
+        st = run_schedule(s, replay, 0, replay.size(), timing, &r);
         if (st != SV_OK) return st;
         r.promotions = 1;
         r.dtype_used = SV_C128;
@@ -515,12 +600,14 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts
 sv_status sv_norm(sv_state *s, double *out) {
     clear_error();
     if (!s || !out) return set_error(SV_ERR_ARG, "sv_norm: null argument");
+    if (check_live(s, "sv_norm") != SV_OK) return SV_ERR_STATE;
     return measure_norm(s, out);
 }
 
 sv_status sv_probs(sv_state *s, void *out, int out_on_device) {
     clear_error();
     if (!s || !out) return set_error(SV_ERR_ARG, "sv_probs: null argument");
+    if (check_live(s, "sv_probs") != SV_OK) return SV_ERR_STATE;
     if (out_on_device) return launch_probs(s, out);
     // Pinned (page-locked, device-mapped) host memory: the kernel writes it directly over
     // the CPU-GPU link, with no device temporary and no separate copy.
@@ -548,6 +635,7 @@ sv_status sv_probs(sv_state *s, void *out, int out_on_device) {
 sv_status sv_density_probs(sv_state *s, void *out, int out_on_device) {
     clear_error();
     if (!s || !out) return set_error(SV_ERR_ARG, "sv_density_probs: null argument");
+    if (check_live(s, "sv_density_probs") != SV_OK) return SV_ERR_STATE;
     if (s->n % 2) return set_error(SV_ERR_ARG, "sv_density_probs: the state is not a vectorised density matrix (odd width)");
     if (out_on_device) return launch_density_probs(s, out);
     cudaPointerAttributes pa;
@@ -576,6 +664,7 @@ sv_status sv_expect(sv_state *s, const uint64_t *xmask, const uint64_t *zmask, c
     clear_error();
     if (!s || !out || (nterms && (!xmask || !zmask || !coef)))
         return set_error(SV_ERR_ARG, "sv_expect: null argument");
+    if (check_live(s, "sv_expect") != SV_OK) return SV_ERR_STATE;
     const uint64_t lim = s->n >= 64 ? ~0ull : ((1ull << s->n) - 1);
     for (size_t t = 0; t < nterms; ++t)
         if ((xmask[t] & ~lim) || (zmask[t] & ~lim))
@@ -592,10 +681,17 @@ sv_status sv_expect(sv_state *s, const uint64_t *xmask, const uint64_t *zmask, c
 sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p) {
     clear_error();
     if (!s || !idx || !p) return set_error(SV_ERR_ARG, "sv_topk: null argument");
+    if (check_live(s, "sv_topk") != SV_OK) return SV_ERR_STATE;
     if (k < 1 || k > 64) return set_error(SV_ERR_ARG, "sv_topk: k must be 1..64");
     sv_status st = launch_topk(s, k, idx, p);
     if (st != SV_OK) return st;
     return check_device_error(s);
+}
+
+sv_status sv_debug_fail_allocs(uint32_t count) {
+    clear_error();
+    g_fail_allocs.store(count);
+    return SV_OK;
 }
 
 sv_status sv_set_policy(sv_state *s, uint32_t flags) {
@@ -610,6 +706,7 @@ sv_status sv_set_policy(sv_state *s, uint32_t flags) {
 sv_status sv_sync(sv_state *s) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_sync: null state");
+    if (check_live(s, "sv_sync") != SV_OK) return SV_ERR_STATE;
     return check_device_error(s);
 }
 

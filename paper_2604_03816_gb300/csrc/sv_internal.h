@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,12 @@ std::vector<Gate> replay_fusion(std::vector<Gate> nodes, const FusePlan &plan);
 struct sv_circuit {
     uint32_t n = 0;
     std::vector<svi::Gate> gates;
+    // the input gates (targets sorted), kept so that complex128 states can run the same
+    // circuit fused at the tensor-core kernel's widest width (4) instead of applying
+    // width-5 gates on the FP64 CUDA cores; that schedule is built on first use
+    std::vector<svi::Gate> in_gates;
+    mutable std::once_flag narrow_once;
+    mutable std::vector<svi::Gate> narrow;
     // how it was fused, for sv_fuse_like: input qubit sets and the recorded plan
     uint32_t max_k = 0;
     uint32_t flags = 0;               // SV_FUSE_* it was fused with
@@ -103,6 +110,11 @@ struct sv_state {
     size_t samp_cap = 0;
 };
 
+namespace svi {
+// Which kernel family ran a pass (launch_apply's optional out-parameter).
+enum PassKind { PASS_CUDA_CORE = 0, PASS_TENSOR_CORE = 1, PASS_STRUCTURED = 2 };
+}  // namespace svi
+
 // One batched launch: gate k/t applied to `states` consecutive states at psi with
 // per-state matrices at utab (batch.cu).
 struct sv_batch_launch {
@@ -127,7 +139,7 @@ namespace svi {
 // ---- kernels (apply_kernels.cu / reduce_kernels.cu); all enqueue on s->stream ----
 // One pass of g; *bytes (if given) gets the pass's algorithmic HBM bytes: a full read and
 // write of the state, or of the amplitudes a structure-aware pass touches.
-sv_status launch_apply(sv_state *s, const Gate &g, uint64_t *bytes = nullptr);
+sv_status launch_apply(sv_state *s, const Gate &g, uint64_t *bytes = nullptr, int *kind = nullptr);
 // Structure-aware pass (apply_struct.cu): is it preferred over the dense kernels, and run it.
 bool struct_preferred(const sv_state *s, const Structure &st);
 sv_status launch_apply_struct(sv_state *s, const Structure &st, uint64_t *bytes);
@@ -145,6 +157,11 @@ sv_status enqueue_topk(sv_state *s, double *host_p, unsigned long long *host_i);
 sv_status launch_widen(sv_state *s, const void *src_c64, void *dst_c128);
 sv_status launch_set_one(sv_state *s, uint64_t x);
 sv_status check_device_error(sv_state *s);   // synchronises; reads and clears the error word
+// The circuit's input gates fused again at width <= 4 when its schedule has width-5 gates
+// (built once per circuit), else its schedule: what complex128 runs on the tensor cores.
+const std::vector<Gate> &narrow_schedule(const sv_circuit *c);
+// SV_ERR_STATE (with a message) when a failed reallocation left the state without a buffer.
+sv_status check_live(const sv_state *s, const char *who);
 sv_status enqueue_expect_sum(const void *psi, uint32_t n, sv_dtype dtype, const uint64_t *x,
                              const uint64_t *z, const double *c, size_t nterms, double *scratch,
                              size_t scratch_doubles, int nb_fixed, double *out_dev,

@@ -36,7 +36,9 @@ EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
            "sv_expect_noalloc"]
 EXPORTS += ["sv_fuse_like", "sv_sample", "sv_fuse_density", "sv_density_probs", "sv_gate_structure",
-            "sv_fuse_ex"]
+            "sv_fuse_ex", "sv_debug_fail_allocs", "sv_set_zero", "sv_shard_plan_create",
+            "sv_shard_plan_free", "sv_shard_plan_info", "sv_shard_plan_step", "sv_shard_pack",
+            "sv_shard_unpack"]
 EXPORTS += ["sv_server_create", "sv_server_submit", "sv_server_poll", "sv_server_get_stats",
             "sv_server_destroy"]
 EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_get_state",
@@ -45,6 +47,7 @@ SV_POLICY_NO_TENSOR_CORES = 1
 SV_POLICY_DENSE_ONLY = 2
 SV_FUSE_COMMUTE = 1
 SV_STRUCT_DENSE, SV_STRUCT_DIAGONAL, SV_STRUCT_MONOMIAL, SV_STRUCT_IDENTITY = 0, 1, 2, 3
+SV_SHARD_APPLY, SV_SHARD_SWAP = 0, 1
 
 
 class SvError(RuntimeError):
@@ -67,7 +70,8 @@ class sv_apply_report(ctypes.Structure):
     _fields_ = [("dtype_used", ctypes.c_int32), ("promotions", ctypes.c_uint32),
                 ("passes", ctypes.c_uint64), ("norm_before", ctypes.c_double),
                 ("norm_after", ctypes.c_double), ("drift", ctypes.c_double),
-                ("bytes", ctypes.c_uint64), ("apply_ms", ctypes.c_double)]
+                ("bytes", ctypes.c_uint64), ("apply_ms", ctypes.c_double),
+                ("tc_passes", ctypes.c_uint64), ("max_k_used", ctypes.c_uint32)]
 
 
 class sv_batch_opts(ctypes.Structure):
@@ -141,6 +145,16 @@ _sig = {
     "sv_density_probs": [_vp, _vp, ctypes.c_int],
     "sv_sync": [_vp],
     "sv_set_policy": [_vp, _u32],
+    "sv_debug_fail_allocs": [_u32],
+    "sv_set_zero": [_vp],
+    "sv_shard_plan_create": [_vp, _u32, _i32, ctypes.POINTER(_vp)],
+    "sv_shard_plan_free": [_vp],
+    "sv_shard_plan_info": [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_u64),
+                           ctypes.POINTER(_u64)],
+    "sv_shard_plan_step": [_vp, ctypes.c_size_t, ctypes.POINTER(_u32), ctypes.POINTER(_u32),
+                           ctypes.POINTER(_u32), ctypes.POINTER(_vp)],
+    "sv_shard_pack": [_vp, _u32, _u32, _u64, _u64, _vp],
+    "sv_shard_unpack": [_vp, _u32, _u32, _u64, _u64, _vp],
     "sv_server_create": [ctypes.POINTER(sv_server_config), ctypes.POINTER(_vp)],
     "sv_server_submit": [_vp, _u32, _i32, ctypes.POINTER(sv_gate), ctypes.c_size_t,
                          ctypes.POINTER(_u64)],
@@ -223,13 +237,18 @@ def gates_from_specs(specs) -> List[Tuple[Tuple[int, ...], np.ndarray]]:
 # --------------------------------------------------------------------------- circuits
 
 class Circuit:
-    def __init__(self, handle: int):
+    """An sv_circuit handle; owned=False for circuits owned by another object (a shard
+    plan's segments), which are not freed here."""
+
+    def __init__(self, handle: int, owned: bool = True, keep=None):
         self.handle = handle
+        self.owned = owned
+        self.keep = keep
 
     def __del__(self):
-        if getattr(self, "handle", None):
+        if getattr(self, "handle", None) and getattr(self, "owned", True):
             _lib.sv_circuit_free(self.handle)
-            self.handle = None
+        self.handle = None
 
     def __len__(self) -> int:
         return sv_circuit_size(self)[0]
@@ -398,7 +417,8 @@ def sv_apply_circuit(s: State, c: Circuit, adaptive: bool = False, drift_thresho
     _check(_lib.sv_apply_circuit(s.handle, c.handle, ctypes.byref(opts), ctypes.byref(rep)))
     return {"dtype_used": rep.dtype_used, "promotions": rep.promotions, "passes": rep.passes,
             "norm_before": rep.norm_before, "norm_after": rep.norm_after, "drift": rep.drift,
-            "bytes": rep.bytes, "apply_ms": rep.apply_ms}
+            "bytes": rep.bytes, "apply_ms": rep.apply_ms, "tc_passes": rep.tc_passes,
+            "max_k_used": rep.max_k_used}
 
 
 def sv_apply_gate(s: State, targets: Sequence[int], u: np.ndarray) -> None:
@@ -486,6 +506,63 @@ def sv_set_policy(s: State, flags: int) -> None:
 
 def sv_sync(s: State) -> None:
     _check(_lib.sv_sync(s.handle))
+
+
+def sv_debug_fail_allocs(count: int) -> None:
+    _check(_lib.sv_debug_fail_allocs(count))
+
+
+def sv_set_zero(s: State) -> None:
+    _check(_lib.sv_set_zero(s.handle))
+
+
+# --------------------------------------------------------------------------- sharding
+
+class ShardPlan:
+    """An sv_shard_plan handle: the steps every rank of a sharded state runs."""
+
+    def __init__(self, handle: int, circuit: Circuit):
+        self.handle = handle
+        self.circuit = circuit          # the plan reads nothing from it later; kept for clarity
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.sv_shard_plan_free(self.handle)
+            self.handle = None
+
+    def info(self) -> Tuple[int, int, int]:
+        """(steps, exchanges, SWAP passes)."""
+        ns, ex, ls = ctypes.c_size_t(), _u64(), _u64()
+        _check(_lib.sv_shard_plan_info(self.handle, ctypes.byref(ns), ctypes.byref(ex), ctypes.byref(ls)))
+        return ns.value, ex.value, ls.value
+
+    def steps(self):
+        """[(kind, local_bit, global_bit, segment Circuit or None)]."""
+        out = []
+        for i in range(self.info()[0]):
+            kind, lb, gb, seg = _u32(), _u32(), _u32(), _vp()
+            _check(_lib.sv_shard_plan_step(self.handle, i, ctypes.byref(kind), ctypes.byref(lb),
+                                           ctypes.byref(gb), ctypes.byref(seg)))
+            c = Circuit(seg.value, owned=False, keep=self) if kind.value == SV_SHARD_APPLY else None
+            out.append((kind.value, lb.value, gb.value, c))
+        return out
+
+
+def sv_shard_plan_create(c: Circuit, g: int, dtype: int) -> ShardPlan:
+    h = _vp()
+    _check(_lib.sv_shard_plan_create(c.handle, g, dtype, ctypes.byref(h)))
+    return ShardPlan(h.value, c)
+
+
+def sv_shard_pack(s: State, bit: int, value: int, offset: int, count: int, dst) -> None:
+    """dst: CUDA tensor (or device pointer) of at least count amplitudes."""
+    p = int(dst.data_ptr()) if hasattr(dst, "data_ptr") else int(dst)
+    _check(_lib.sv_shard_pack(s.handle, bit, value, offset, count, p))
+
+
+def sv_shard_unpack(s: State, bit: int, value: int, offset: int, count: int, src) -> None:
+    p = int(src.data_ptr()) if hasattr(src, "data_ptr") else int(src)
+    _check(_lib.sv_shard_unpack(s.handle, bit, value, offset, count, p))
 
 
 # --------------------------------------------------------------------------- batches

@@ -130,6 +130,8 @@ def test_qft_brickwork_24q_fused(gpu, qft_brickwork_24q, dtype, k):
     psi, rep = run_gpu(sv, 24, sv.gates_from_specs(specs), dtype, k, x=x)
     check(psi, ref, dtype)
     assert rep["passes"] < len(specs)
+    # complex128 runs a width-5 schedule fused again at width 4 (tensor-core passes)
+    assert rep["max_k_used"] == (min(k, 4) if dtype == 1 else k)
 
 
 @pytest.mark.parametrize("dtype,k", [(0, 5), (1, 4)])
@@ -141,9 +143,11 @@ def test_qft_brickwork_24q_mirror(gpu, dtype, k):
 
 
 @pytest.mark.parametrize("n,dtype,k,cycles", [(30, 0, 4, 24), (30, 0, 5, 24), (33, 0, 5, 24),
-                                              (30, 1, 3, 8), (32, 1, 2, 4)])
+                                              (30, 1, 4, 24), (30, 1, 5, 24), (32, 1, 4, 24)])
 def test_grid_random_mirror_large(gpu, n, dtype, k, cycles):
-    """30/32/33 qubits (oracle too large): the mirror circuit C C^dagger |0> = |0>."""
+    """30/32/33 qubits at the stated depth and widths: the mirror circuit C C^dagger |0> =
+    |0> (Eq. 10 applied to C followed by its inverse).  The forward states themselves are
+    compared element by element in test_gpu_large.py."""
     sv = gpu
     torch = _torch()
     specs = W.grid_random(n, cycles)
@@ -395,3 +399,69 @@ def test_probs_into_pinned_host_memory(gpu, dtype):
         assert np.array_equal(pinned.numpy(), pageable)
         assert np.array_equal(pageable, oracle.probs_in_precision(psi0))
         s.free()
+
+
+def test_c128_width5_circuit_runs_on_the_tensor_cores(gpu):
+    """A circuit fused at width 5, applied to a complex128 state: the state runs the input
+    gates fused at width 4, every pass on the complex128 tensor-core kernel, and matches
+    the oracle at 1e-12; an adaptive complex64 run that drifts replays the same way."""
+    sv = gpu
+    n = 20
+    specs = W.grid_random(n, 8)
+    gl = sv.gates_from_specs(specs)
+    ref = oracle.simulate(n, specs, x=5)
+    c5 = sv.sv_fuse(gl, n, 5)
+    c4 = sv.sv_fuse(gl, n, 4)
+    s = sv.sv_alloc(n, 1, stream=_torch().cuda.current_stream())
+    sv.sv_set_basis(s, 5)
+    rep = sv.sv_apply_circuit(s, c5)
+    assert rep["max_k_used"] == 4 and rep["passes"] == len(c4)
+    assert rep["tc_passes"] == rep["passes"]
+    check(sv.sv_get_state(s), ref, 1)
+    s.free()
+    # promotion: a leaky gate makes the complex64 norm drift; the replay is complex128 at k = 4
+    leak = ((2,), np.diag([1.0 + 1e-4, 1.0]).astype(np.complex128))
+    ogl = OG.gate_list(specs)
+    half = len(gl) // 2
+    ref2 = oracle.run(oracle.basis(n, 5), ogl[:half] + [leak] + ogl[half:])
+    cl = sv.sv_fuse(gl[:half] + [leak] + gl[half:], n, 5)
+    psi, rep2 = run_gpu(sv, n, gl[:half] + [leak] + gl[half:], 0, 5, x=5, adaptive=True)
+    assert rep2["promotions"] == 1 and rep2["dtype_used"] == 1 and rep2["max_k_used"] == 4
+    check(psi, ref2, 1)
+    assert len(cl) < rep2["passes"]
+
+
+def test_promotion_allocation_failure_leaves_a_checked_state(gpu):
+    """Out of memory during a promotion (forced through the library's allocation test
+    hook): the call fails with SV_ERR_OOM, later calls on the state return SV_ERR_STATE
+    instead of launching on a missing buffer, sv_set_dtype recovers it; with only the first
+    allocation failing, the promotion releases the complex64 buffer first and succeeds."""
+    sv = gpu
+    n = 16
+    specs = W.brickwork(n, 4)
+    leak = ((0,), np.diag([1.0 + 1e-3, 1.0]).astype(np.complex128))
+    gl = sv.gates_from_specs(specs) + [leak]
+    ref = oracle.run(oracle.basis(n, 0), OG.gate_list(specs) + [leak])
+    c = sv.sv_fuse(gl, n, 4)
+    s = sv.sv_alloc(n, 0, stream=_torch().cuda.current_stream())
+    try:
+        sv.sv_debug_fail_allocs(2)
+        with pytest.raises(sv.SvError) as e:
+            sv.sv_apply_circuit(s, c, adaptive=True)
+        assert e.value.status == 2
+        sv.sv_debug_fail_allocs(0)
+        for call in (lambda: sv.sv_norm(s), lambda: sv.sv_topk(s, 4), lambda: sv.sv_probs(s),
+                     lambda: sv.sv_apply_circuit(s, c), lambda: sv.sv_set_basis(s, 1),
+                     lambda: sv.sv_get_state(s), lambda: sv.sv_sample(s, 1, 4)):
+            with pytest.raises(sv.SvError) as e:
+                call()
+            assert e.value.status == 5
+        sv.sv_set_dtype(s, 0)
+        assert abs(sv.sv_norm(s) - 1.0) < 1e-7 and sv.sv_info(s)[1] == 0
+        sv.sv_debug_fail_allocs(1)
+        rep = sv.sv_apply_circuit(s, c, adaptive=True)
+        assert rep["promotions"] == 1 and sv.sv_info(s)[1] == 1
+        check(sv.sv_get_state(s), ref, 1)
+    finally:
+        sv.sv_debug_fail_allocs(0)
+    s.free()

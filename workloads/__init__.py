@@ -299,14 +299,15 @@ class Request:
 
 
 def serving_stream(rate_hz: float, duration_s: float, seed: Optional[int] = None,
-                   width_range=(10, 30), depth_range=(10, 60), frac_c64: float = 0.7
-                   ) -> List[Request]:
-    """Poisson arrivals of brickwork circuits of width ~ U{10..30}, depth ~ U{10..60}."""
+                   width_range=(10, 30), depth_range=(10, 60), frac_c64: float = 0.7,
+                   max_requests: Optional[int] = None) -> List[Request]:
+    """Poisson arrivals of brickwork circuits of width ~ U{10..30}, depth ~ U{10..60}:
+    the arrivals within duration_s, at most max_requests of them."""
     rng = np.random.default_rng(seed_for(5, int(rate_hz)) if seed is None else seed)
     t = 0.0
     out: List[Request] = []
     i = 0
-    while True:
+    while max_requests is None or i < max_requests:
         t += float(rng.exponential(1.0 / rate_hz))
         if t > duration_s:
             break
