@@ -577,7 +577,8 @@ def run_batched(args, steps=None, warmup=None):
                 circs = ahead[0].result() if w == order[0] else fuse_width(w)
                 fuse_s += time.perf_counter() - t0
                 sv.sv_batch_set_basis(batches[w], 0)
-                sv.sv_batch_apply(batches[w], circs, l2_bytes=tune[w]["l2_bytes"])
+                sv.sv_batch_apply(batches[w], circs, l2_bytes=tune[w]["l2_bytes"],
+                                  tile_bits=tune[w].get("tile_bits", 0))
             ahead[0] = fuser.submit(fuse_width, order[0])
             for w in widths:
                 xs, zs, cs = W.zz_chain(w)
@@ -624,6 +625,7 @@ def run_batched(args, steps=None, warmup=None):
                       "per_width": {str(w): {"circuits": len(groups[w]),
                                              "best_k": tune[w]["best_k"],
                                              "l2_chunk_bytes": tune[w]["l2_bytes"],
+                                             "tile_bits": tune[w].get("tile_bits", 0),
                                              "tune_ms": tune[w]["ms"]} for w in widths}},
            "host_fusion_s_per_step": fuse_total / steps,
            "unbatched_circuits_per_s": unb,

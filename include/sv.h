@@ -315,6 +315,8 @@ typedef struct {
     uint32_t timing;         /* 1: time the passes with CUDA events (synchronises) */
     uint32_t no_tensor_cores; /* 1: complex64 width-4/5 gates on the CUDA cores too (default:
                                  on the tensor cores when n >= 12) */
+    uint32_t tile_bits;      /* CUDA-core passes: tiles of 2^tile_bits amplitudes per CTA,
+                                10..13 (0: 12 for complex64, 11 for complex128) */
 } sv_batch_opts;
 
 typedef struct {
@@ -324,6 +326,7 @@ typedef struct {
     uint32_t chunk_states;
     uint32_t graph_reused;   /* 1 if a previously captured graph was replayed */
     double apply_ms;         /* with opts->timing */
+    uint32_t tile_bits;      /* tile size of the CUDA-core passes */
 } sv_batch_report;
 
 typedef struct {
@@ -332,6 +335,7 @@ typedef struct {
     double best_ms;
     double ms[SV_MAX_K + 1]; /* best time per width (index k), 0 if not tried */
     uint32_t cached;         /* 1 if the answer came from the cache */
+    uint32_t tile_bits;      /* tile size of the CUDA-core passes (0: the default) */
 } sv_tune_result;
 
 /* count in 1..65535; dev_buf: caller buffer of >= count * 2^n * s bytes or NULL.  All
@@ -353,9 +357,11 @@ sv_status sv_batch_expect(sv_batch *b, const uint64_t *xmask, const uint64_t *zm
 sv_status sv_batch_sync(sv_batch *b);
 /* Autotuner: fuse `gates` (one representative circuit of the family) at every width
  * kmin..kmax, time the batched apply on this batch for three chunk budgets (64 MiB,
- * 512 MiB, the whole batch), and return the fastest; results are cached per batch shape and target
- * sequence (the measure-once-and-cache idea of Algorithm 1, applied to the fusion width
- * and the chunking).  Overwrites the batch's states with |0...0>.  Synchronises. */
+ * 512 MiB, the whole batch) and, when the schedule has CUDA-core passes, for every tile
+ * size 10..13 at the width's best chunking; return the fastest (width, chunk budget, tile
+ * size).  Results are cached per batch shape and target sequence (the
+ * measure-once-and-cache idea of Algorithm 1, applied to the fusion width, the chunking
+ * and the tile shape).  Overwrites the batch's states with |0...0>.  Synchronises. */
 sv_status sv_batch_tune(sv_batch *b, const sv_gate *gates, size_t ngates, uint32_t kmin, uint32_t kmax,
                         sv_tune_result *out);
 

@@ -156,32 +156,39 @@ constexpr uint32_t batch_tile_bits() {
     return sizeof(R) == 4 ? 12u : 11u;
 }
 
+// Tile sizes the batched CUDA-core kernel accepts (2^TB amplitudes per CTA); the
+// autotuner may pick any of them per batch.
+constexpr uint32_t BATCH_TB_MIN = 10, BATCH_TB_MAX = 13;
+
 template <typename R, int K>
 struct BatchKernel {
-    static cudaError_t prepare(int *blocks_per_sm) {
+    // The dynamic shared-memory limit is set for the largest tile once; the resident CTAs
+    // per SM are measured per tile size.
+    static cudaError_t prepare(uint32_t tb, int *blocks_per_sm) {
         static std::once_flag once;
-        static int bps = 1;
+        static int bps[BATCH_TB_MAX + 1] = {};
         static cudaError_t err = cudaSuccess;
         std::call_once(once, [] {
             using C = typename BC2<R>::T;
-            const int maxb = int((1u << batch_tile_bits<R, K>()) * sizeof(C));
-            err = cudaFuncSetAttribute(apply_batch_tile<R, K>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, maxb);
-            if (err == cudaSuccess)
-                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, apply_batch_tile<R, K>,
-                                                                    256, maxb);
-            if (bps < 1) bps = 1;
+            err = cudaFuncSetAttribute(apply_batch_tile<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int((1u << BATCH_TB_MAX) * sizeof(C)));
+            for (uint32_t t = BATCH_TB_MIN; t <= BATCH_TB_MAX && err == cudaSuccess; ++t) {
+                err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps[t], apply_batch_tile<R, K>, 256,
+                                                                    int((1u << t) * sizeof(C)));
+                if (bps[t] < 1) bps[t] = 1;
+            }
         });
-        *blocks_per_sm = bps;
+        *blocks_per_sm = bps[tb];
         return err;
     }
     static sv_status launch(const sv_batch_launch &L) {
         using C = typename BC2<R>::T;
+        const uint32_t tb = L.tile_bits ? L.tile_bits : batch_tile_bits<R, K>();
         int bps = 1;
-        const cudaError_t e = prepare(&bps);
+        const cudaError_t e = prepare(tb, &bps);
         if (e != cudaSuccess)
             return svi::set_error(SV_ERR_CUDA, std::string("batch kernel setup: ") + cudaGetErrorString(e));
-        const Plan p = make_plan(L.n, K, L.t, batch_tile_bits<R, K>());
+        const Plan p = make_plan(L.n, K, L.t, tb);
         BatchArgs<K> a;
         a.utab = L.utab;
         a.psi = L.psi;
@@ -362,19 +369,19 @@ static cudaError_t batch_prepare(sv_dtype dt, uint32_t k) {
     int bps = 0;
     if (dt == SV_C64) {
         switch (k) {
-            case 1: return svk::BatchKernel<float, 1>::prepare(&bps);
-            case 2: return svk::BatchKernel<float, 2>::prepare(&bps);
-            case 3: return svk::BatchKernel<float, 3>::prepare(&bps);
-            case 4: return svk::BatchKernel<float, 4>::prepare(&bps);
-            default: return svk::BatchKernel<float, 5>::prepare(&bps);
+            case 1: return svk::BatchKernel<float, 1>::prepare(svk::BATCH_TB_MAX, &bps);
+            case 2: return svk::BatchKernel<float, 2>::prepare(svk::BATCH_TB_MAX, &bps);
+            case 3: return svk::BatchKernel<float, 3>::prepare(svk::BATCH_TB_MAX, &bps);
+            case 4: return svk::BatchKernel<float, 4>::prepare(svk::BATCH_TB_MAX, &bps);
+            default: return svk::BatchKernel<float, 5>::prepare(svk::BATCH_TB_MAX, &bps);
         }
     }
     switch (k) {
-        case 1: return svk::BatchKernel<double, 1>::prepare(&bps);
-        case 2: return svk::BatchKernel<double, 2>::prepare(&bps);
-        case 3: return svk::BatchKernel<double, 3>::prepare(&bps);
-        case 4: return svk::BatchKernel<double, 4>::prepare(&bps);
-        default: return svk::BatchKernel<double, 5>::prepare(&bps);
+        case 1: return svk::BatchKernel<double, 1>::prepare(svk::BATCH_TB_MAX, &bps);
+        case 2: return svk::BatchKernel<double, 2>::prepare(svk::BATCH_TB_MAX, &bps);
+        case 3: return svk::BatchKernel<double, 3>::prepare(svk::BATCH_TB_MAX, &bps);
+        case 4: return svk::BatchKernel<double, 4>::prepare(svk::BATCH_TB_MAX, &bps);
+        default: return svk::BatchKernel<double, 5>::prepare(svk::BATCH_TB_MAX, &bps);
     }
 }
 
@@ -582,13 +589,16 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
     chunk = std::min(chunk, b->count);
     const bool use_graph = !(opts && opts->no_graph);
     const bool timing = opts && opts->timing;
+    const uint32_t tile_bits = opts ? opts->tile_bits : 0u;
+    if (tile_bits && (tile_bits < svk::BATCH_TB_MIN || tile_bits > svk::BATCH_TB_MAX))
+        return set_error(SV_ERR_ARG, "sv_batch_apply: tile_bits must be 0 or 10..13");
     // complex64 gates of width 4 and 5 on the tensor cores (states of at least 12 qubits)
     const bool tc_ok = b->dtype == SV_C64 && b->n >= 12 && !(opts && opts->no_tensor_cores);
     auto use_tc = [&](const Gate &g) { return tc_ok && (g.k == 4 || g.k == 5); };
 
     std::string key = std::to_string(b->n) + "/" + std::to_string(b->count) + "/" +
                       std::to_string(b->dtype) + "/" + std::to_string(chunk) + "/" +
-                      (tc_ok ? "tc/" : "cc/");
+                      (tc_ok ? "tc/" : "cc/") + std::to_string(tile_bits) + "/";
     for (const Gate &g : c0->gates)
         for (uint32_t j = 0; j < g.k; ++j) key += std::to_string(g.t[j]) + (j + 1 < g.k ? "," : ";");
 
@@ -610,6 +620,7 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
                 L.stream = stream;
                 L.num_sms = b->num_sms;
                 L.tc = use_tc(gg);
+                L.tile_bits = tile_bits;
                 sv_status st = batch_launch(L);
                 if (st != SV_OK) return st;
             }
@@ -620,6 +631,7 @@ sv_status sv_batch_apply(sv_batch *b, const sv_circuit *const *circuits, const s
     sv_batch_report r;
     std::memset(&r, 0, sizeof(r));
     r.chunk_states = chunk;
+    r.tile_bits = tile_bits ? tile_bits : (b->dtype == SV_C64 ? 12u : 11u);
     r.passes = (uint64_t)G * b->count;
     r.launches = (uint64_t)G * ((b->count + chunk - 1) / chunk);
     r.bytes = (uint64_t)G * b->count * 2ull * sbytes;
@@ -752,31 +764,49 @@ sv_status sv_batch_tune(sv_batch *b, const sv_gate *gates, size_t ngates, uint32
     // (a fixed cost of about 20 us per launch) prefer few large launches
     const size_t sbytes = (b->dtype == SV_C64 ? size_t(8) : size_t(16)) << b->n;
     const size_t l2s[3] = {size_t(64) << 20, size_t(512) << 20, sbytes * b->count};
+    const bool tc_ok = b->dtype == SV_C64 && b->n >= 12;
     for (uint32_t k = kmin; k <= kmax; ++k) {
         sv_circuit *c = nullptr;
         sv_status st = sv_fuse(gates, ngates, b->n, k, &c);
         if (st != SV_OK) return st;
         std::vector<const sv_circuit *> cs(b->count, c);
         double kbest = 1e300;
-        for (size_t l2 : l2s) {
+        size_t kl2 = l2s[0];
+        auto time_it = [&](size_t l2, uint32_t tb) -> double {
             sv_batch_opts o;
             std::memset(&o, 0, sizeof(o));
             o.l2_bytes = l2;
             o.timing = 1;
+            o.tile_bits = tb;
             sv_batch_report rep;
             double ms = 1e300;
             for (int rep_i = 0; rep_i < 3 && st == SV_OK; ++rep_i) {   // first run warms up
                 st = sv_batch_apply(b, cs.data(), &o, &rep);
                 if (rep_i > 0) ms = std::min(ms, rep.apply_ms);
             }
-            if (st != SV_OK) break;
-            if (ms < kbest) kbest = ms;
-            if (ms < best) {
+            if (st == SV_OK && ms < best) {
                 best = ms;
                 r.best_k = k;
                 r.l2_bytes = l2;
+                r.tile_bits = tb;
+            }
+            return ms;
+        };
+        for (size_t l2 : l2s) {
+            const double ms = time_it(l2, 0);
+            if (st != SV_OK) break;
+            if (ms < kbest) {
+                kbest = ms;
+                kl2 = l2;
             }
         }
+        // the tile size of the CUDA-core passes, at this width's best chunking, when the
+        // schedule has such passes (complex128, narrow gates, tensor cores not eligible)
+        bool cuda_core = false;
+        for (const Gate &g : c->gates) cuda_core = cuda_core || !(tc_ok && (g.k == 4 || g.k == 5));
+        if (cuda_core && st == SV_OK)
+            for (uint32_t tb = svk::BATCH_TB_MIN; tb <= svk::BATCH_TB_MAX && st == SV_OK; ++tb)
+                kbest = std::min(kbest, time_it(kl2, tb));
         sv_circuit_free(c);
         if (st != SV_OK) return st;
         r.ms[k] = kbest;

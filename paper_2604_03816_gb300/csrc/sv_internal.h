@@ -128,6 +128,7 @@ struct sv_batch_launch {
     cudaStream_t stream = nullptr;
     int num_sms = 0;
     bool tc = false;            // complex64 width 4/5 on the tensor cores (apply_tc.cu)
+    uint32_t tile_bits = 0;     // CUDA-core passes: 2^tile_bits amplitudes per CTA (0: default)
 };
 
 namespace svk {

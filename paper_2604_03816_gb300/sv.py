@@ -77,19 +77,20 @@ class sv_apply_report(ctypes.Structure):
 class sv_batch_opts(ctypes.Structure):
     _fields_ = [("chunk_states", ctypes.c_uint32), ("l2_bytes", ctypes.c_size_t),
                 ("no_graph", ctypes.c_uint32), ("timing", ctypes.c_uint32),
-                ("no_tensor_cores", ctypes.c_uint32)]
+                ("no_tensor_cores", ctypes.c_uint32), ("tile_bits", ctypes.c_uint32)]
 
 
 class sv_batch_report(ctypes.Structure):
     _fields_ = [("passes", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("bytes", ctypes.c_uint64), ("chunk_states", ctypes.c_uint32),
-                ("graph_reused", ctypes.c_uint32), ("apply_ms", ctypes.c_double)]
+                ("graph_reused", ctypes.c_uint32), ("apply_ms", ctypes.c_double),
+                ("tile_bits", ctypes.c_uint32)]
 
 
 class sv_tune_result(ctypes.Structure):
     _fields_ = [("best_k", ctypes.c_uint32), ("l2_bytes", ctypes.c_size_t),
                 ("best_ms", ctypes.c_double), ("ms", ctypes.c_double * (SV_MAX_K + 1)),
-                ("cached", ctypes.c_uint32)]
+                ("cached", ctypes.c_uint32), ("tile_bits", ctypes.c_uint32)]
 
 
 class sv_server_config(ctypes.Structure):
@@ -609,16 +610,16 @@ def sv_batch_get_state(b: Batch, i: int) -> np.ndarray:
 
 def sv_batch_apply(b: Batch, circuits: Sequence[Circuit], chunk_states: int = 0,
                    l2_bytes: int = 0, no_graph: bool = False, timing: bool = False,
-                   no_tensor_cores: bool = False) -> dict:
+                   no_tensor_cores: bool = False, tile_bits: int = 0) -> dict:
     arr = (_vp * len(circuits))(*[c.handle for c in circuits])
     assert len(circuits) == b.count
     opts = sv_batch_opts(chunk_states, l2_bytes, int(bool(no_graph)), int(bool(timing)),
-                         int(bool(no_tensor_cores)))
+                         int(bool(no_tensor_cores)), tile_bits)
     rep = sv_batch_report()
     _check(_lib.sv_batch_apply(b.handle, arr, ctypes.byref(opts), ctypes.byref(rep)))
     return {"passes": rep.passes, "launches": rep.launches, "bytes": rep.bytes,
             "chunk_states": rep.chunk_states, "graph_reused": rep.graph_reused,
-            "apply_ms": rep.apply_ms}
+            "apply_ms": rep.apply_ms, "tile_bits": rep.tile_bits}
 
 
 def sv_batch_expect(b: Batch, xmask, zmask, coef) -> np.ndarray:
@@ -642,7 +643,8 @@ def sv_batch_tune(b: Batch, gates: Sequence[Tuple[Sequence[int], np.ndarray]], k
     r = sv_tune_result()
     _check(_lib.sv_batch_tune(b.handle, ga.arr, ga.n, kmin, kmax, ctypes.byref(r)))
     return {"best_k": r.best_k, "l2_bytes": r.l2_bytes, "best_ms": r.best_ms,
-            "ms": {k: r.ms[k] for k in range(kmin, kmax + 1)}, "cached": r.cached}
+            "ms": {k: r.ms[k] for k in range(kmin, kmax + 1)}, "cached": r.cached,
+            "tile_bits": r.tile_bits}
 
 
 # --------------------------------------------------------------------------- serving

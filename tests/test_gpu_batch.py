@@ -87,8 +87,36 @@ def test_batch_tune_picks_and_caches(gpu):
     assert r["best_ms"] == min(r["ms"].values())
     r2 = sv.sv_batch_tune(b, gl, 1, 4)
     assert r2["cached"] == 1 and r2["best_k"] == r["best_k"]
+    assert r2["tile_bits"] == r["tile_bits"] and r["tile_bits"] in (0, 10, 11, 12, 13)
     # the states were reset to |0...0>
     assert sv.sv_batch_get_state(b, 0)[0] == 1
+    b.free()
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_batch_tile_sizes_give_identical_states(gpu, dtype):
+    """The CUDA-core batched passes at every tile size the tuner may choose (2^10..2^13
+    amplitudes per CTA): each group's arithmetic is the same, so the states agree bit for
+    bit across tile sizes and with the oracle."""
+    sv = gpu
+    import torch
+    n, count = 15, 6
+    fam = [W.hea(n, 3, seed=40 + i) for i in range(count)]
+    circs = [sv.sv_fuse(sv.gates_from_specs(f), n, 3) for f in fam]
+    b = sv.sv_batch_alloc(n, dtype, count, stream=torch.cuda.current_stream())
+    states = {}
+    for tb in (0, 10, 11, 12, 13):
+        sv.sv_batch_set_basis(b, 0)
+        rep = sv.sv_batch_apply(b, circs, tile_bits=tb, no_tensor_cores=True)
+        assert rep["tile_bits"] == (tb or (12 if dtype == 0 else 11))
+        states[tb] = [sv.sv_batch_get_state(b, i) for i in range(count)]
+    for tb in (10, 11, 12, 13):
+        assert all(np.array_equal(a, z) for a, z in zip(states[0], states[tb])), tb
+    tol = 1e-5 if dtype == 0 else 1e-12
+    for i, f in enumerate(fam):
+        assert np.max(np.abs(states[13][i].astype(np.complex128) - oracle.simulate(n, f))) < tol
+    with pytest.raises(sv.SvError):
+        sv.sv_batch_apply(b, circs, tile_bits=9)
     b.free()
 
 

@@ -100,3 +100,38 @@ def test_admission_prefers_short_requests(gpu):
     assert all(r["status"] == 0 for r in got.values())
     assert got[b0]["t_admit"] < got[b1]["t_admit"]
     assert max(got[i]["t_admit"] for i in ids) < got[b1]["t_admit"]
+
+
+def test_large_complex128_requests_under_a_budget_of_a_few_states(gpu):
+    """28-30-qubit complex128 requests (4-16 GiB each) against a 40 GiB budget: the bytes
+    in use never exceed the budget, requests queue while it is full, and every result is
+    the one the same request gives alone."""
+    sv = gpu
+    budget = 40 << 30
+    reqs = [(30, 1, 1), (30, 1, 2), (29, 1, 3), (28, 1, 4), (30, 1, 5), (29, 0, 6)]
+    arrays = [sv.GateArray(sv.gates_from_specs(W.brickwork(n, 5, seed=s))) for n, _, s in reqs]
+    srv = sv.sv_server_create(budget_bytes=budget, max_slots=8, max_k=4)
+    alone = []
+    for (n, dt, _), ga in zip(reqs, arrays):
+        rid = sv.sv_server_submit(srv, n, dt, ga)
+        alone.append(_drain(sv, srv, 1, timeout_s=300)[rid])
+    ids = [sv.sv_server_submit(srv, n, dt, ga) for (n, dt, _), ga in zip(reqs, arrays)]
+    got, peak, t0 = {}, 0, time.time()
+    while len(got) < len(ids):
+        st = sv.sv_server_get_stats(srv)
+        assert st["in_use_bytes"] <= budget
+        peak = max(peak, st["in_use_bytes"])
+        for r in sv.sv_server_poll(srv, 64, 5):
+            got[r["id"]] = r
+        assert time.time() - t0 < 300
+    srv.destroy()
+    assert peak > (16 << 30)                             # several large states at once
+    for a, rid in zip(alone, ids):
+        m = got[rid]
+        assert a["status"] == 0 and m["status"] == 0
+        assert np.array_equal(a["idx"], m["idx"]) and np.array_equal(a["p"], m["p"])
+    # two 30-qubit complex128 states (16 GiB each) fit the budget, three do not: the
+    # last of the three is admitted only after one of the others has finished
+    big = sorted((got[rid] for rid, (n, dt, _) in zip(ids, reqs) if n == 30 and dt == 1),
+                 key=lambda r: r["t_admit"])
+    assert big[2]["t_admit"] >= min(big[0]["t_done"], big[1]["t_done"])
