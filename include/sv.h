@@ -294,6 +294,11 @@ sv_status sv_gate_structure(const sv_gate *g, uint32_t *kind, uint32_t *control_
  * kernels, everything else on the CUDA cores). */
 #define SV_POLICY_NO_TENSOR_CORES 1u   /* always use the CUDA-core kernels */
 #define SV_POLICY_DENSE_ONLY 2u        /* ignore gate structure: every gate a dense pass */
+/* sv_probs into page-locked host memory goes through a device buffer of the probabilities'
+ * size (2^n * 4 or 8 bytes, allocated on first use and kept by the state until sv_free) and
+ * one copy-engine transfer, instead of the kernel writing over the CPU-GPU link itself: the
+ * transfer then occupies no SM, so passes of states on other streams run meanwhile. */
+#define SV_POLICY_STAGED_PROBS 4u
 sv_status sv_set_policy(sv_state *s, uint32_t flags);
 
 /* ------------------------------------------------------------ batched execution */

@@ -190,6 +190,7 @@ sv_status sv_free(sv_state *s) {
     if (s->ws) cudaFree(s->ws);
     if (s->snap) cudaFree(s->snap);
     if (s->samp) cudaFree(s->samp);
+    if (s->probs_buf) cudaFree(s->probs_buf);
     delete s;
     return SV_OK;
 }
@@ -609,17 +610,35 @@ sv_status sv_probs(sv_state *s, void *out, int out_on_device) {
     if (!s || !out) return set_error(SV_ERR_ARG, "sv_probs: null argument");
     if (check_live(s, "sv_probs") != SV_OK) return SV_ERR_STATE;
     if (out_on_device) return launch_probs(s, out);
-    // Pinned (page-locked, device-mapped) host memory: the kernel writes it directly over
-    // the CPU-GPU link, with no device temporary and no separate copy.
     cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-        pa.devicePointer != nullptr) {
+    const bool pinned = cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+                        pa.devicePointer != nullptr;
+    (void)cudaGetLastError();   // a pageable pointer is not an error
+    const size_t pbytes = size_t(s->dtype == SV_C64 ? 4 : 8) << s->n;
+    if (pinned && (s->policy & SV_POLICY_STAGED_PROBS)) {
+        // through a device buffer kept by the state and one copy-engine transfer: the
+        // kernel is a short HBM pass and the link transfer occupies no SM, so passes of
+        // other streams run meanwhile
+        if (s->probs_cap < pbytes) {
+            if (s->probs_buf) cudaFree(s->probs_buf);
+            s->probs_buf = nullptr;
+            s->probs_cap = 0;
+            SV_CUDA(cudaMalloc(&s->probs_buf, pbytes));
+            s->probs_cap = pbytes;
+        }
+        sv_status st = launch_probs(s, s->probs_buf);
+        if (st != SV_OK) return st;
+        SV_CUDA(cudaMemcpyAsync(out, s->probs_buf, pbytes, cudaMemcpyDeviceToHost, s->stream));
+        return check_device_error(s);
+    }
+    if (pinned) {
+        // Pinned (page-locked, device-mapped) host memory: the kernel writes it directly
+        // over the CPU-GPU link, with no device temporary and no separate copy.
         const sv_status st = launch_probs(s, pa.devicePointer);
         if (st != SV_OK) return st;
         return check_device_error(s);
     }
-    (void)cudaGetLastError();   // a pageable pointer is not an error
-    const size_t bytes = size_t(s->dtype == SV_C64 ? 4 : 8) << s->n;
+    const size_t bytes = pbytes;
     void *tmp = nullptr;
     SV_CUDA(cudaMallocAsync(&tmp, bytes, s->stream));
     sv_status st = launch_probs(s, tmp);
@@ -697,7 +716,7 @@ sv_status sv_debug_fail_allocs(uint32_t count) {
 sv_status sv_set_policy(sv_state *s, uint32_t flags) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_set_policy: null state");
-    if (flags & ~(SV_POLICY_NO_TENSOR_CORES | SV_POLICY_DENSE_ONLY))
+    if (flags & ~(SV_POLICY_NO_TENSOR_CORES | SV_POLICY_DENSE_ONLY | SV_POLICY_STAGED_PROBS))
         return set_error(SV_ERR_ARG, "sv_set_policy: unknown flag");
     s->policy = flags;
     return SV_OK;

@@ -108,6 +108,8 @@ struct sv_state {
     uint32_t policy = 0;        // SV_POLICY_* flags (kernel selection)
     void *samp = nullptr;       // sampling scratch (sample.cu), kept across calls
     size_t samp_cap = 0;
+    void *probs_buf = nullptr;  // SV_POLICY_STAGED_PROBS: device probabilities, kept across calls
+    size_t probs_cap = 0;
 };
 
 namespace svi {

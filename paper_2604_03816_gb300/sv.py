@@ -45,6 +45,7 @@ EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_g
             "sv_batch_apply", "sv_batch_expect", "sv_batch_sync", "sv_batch_tune"]
 SV_POLICY_NO_TENSOR_CORES = 1
 SV_POLICY_DENSE_ONLY = 2
+SV_POLICY_STAGED_PROBS = 4
 SV_FUSE_COMMUTE = 1
 SV_STRUCT_DENSE, SV_STRUCT_DIAGONAL, SV_STRUCT_MONOMIAL, SV_STRUCT_IDENTITY = 0, 1, 2, 3
 SV_SHARD_APPLY, SV_SHARD_SWAP = 0, 1

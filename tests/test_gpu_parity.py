@@ -398,6 +398,12 @@ def test_probs_into_pinned_host_memory(gpu, dtype):
         sv.sv_probs(s, pinned.numpy())
         assert np.array_equal(pinned.numpy(), pageable)
         assert np.array_equal(pageable, oracle.probs_in_precision(psi0))
+        # staged through a device buffer and a copy-engine transfer: the same bits
+        sv.sv_set_policy(s, sv.SV_POLICY_STAGED_PROBS)
+        for _ in range(2):
+            pinned.fill_(-1.0)
+            sv.sv_probs(s, pinned.numpy())
+            assert np.array_equal(pinned.numpy(), pageable)
         s.free()
 
 
