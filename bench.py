@@ -875,8 +875,9 @@ def main():
         rep = sv.sv_apply_circuit(state, c, adaptive=True, timing=timing)
         idx, p = sv.sv_topk(state, 64)
         zz = sv.sv_expect(state, [0], [3], [1.0])
-        # kernels: passes + 2 x norm (2 each) + set_basis (1) + top-k (2) + expect (2)
-        launches_per_step[0] = rep["passes"] + 4 * (1 + rep["promotions"]) + 1 + 2 + 2
+        # kernels: passes + the norm after the run (2; a basis start needs none before it,
+        # a promotion adds one) + set_basis (1) + top-k (2) + expect (2)
+        launches_per_step[0] = rep["passes"] + 2 * (1 + rep["promotions"]) + 1 + 2 + 2
         return rep, len(c), (idx, p, zz)
 
     with torch.cuda.stream(stream):

@@ -175,7 +175,8 @@ typedef struct {
     int32_t dtype_used;         /* sv_dtype that produced the final state */
     uint32_t promotions;        /* 1 if the circuit was replayed in complex128 */
     uint64_t passes;            /* gate passes enqueued (including a replay) */
-    double norm_before;         /* FP64 norms measured when adaptive (else 0) */
+    double norm_before;         /* FP64 norms when adaptive (else 0); norm_before of a basis
+                                   start is exactly 1 and takes no pass */
     double norm_after;
     double drift;               /* |norm_after - norm_before| of the reported run */
     uint64_t bytes;             /* algorithmic HBM bytes of the passes: 2 * 2^n * s per dense

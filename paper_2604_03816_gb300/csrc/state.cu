@@ -551,7 +551,9 @@ sv_status sv_apply_circuit(sv_state *s, const sv_circuit *c, const sv_apply_opts
         }
         SV_CUDA(cudaMemcpyAsync(s->snap, s->buf, bytes64, cudaMemcpyDeviceToDevice, s->stream));
     }
-    sv_status st = measure_norm(s, &r.norm_before);
+    // a basis state |x> holds one amplitude 1 + 0i: its norm is exactly 1, no pass needed
+    sv_status st = from_basis ? SV_OK : measure_norm(s, &r.norm_before);
+    if (from_basis) r.norm_before = 1.0;
     if (st != SV_OK) return st;
     s->basis_known = false;
     bool promote = false;

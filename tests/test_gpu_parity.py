@@ -256,9 +256,10 @@ def test_adaptive_promotion_replays_in_c128(gpu):
     sv.sv_apply_circuit(s, c)
     check(sv.sv_get_state(s).astype(np.complex128), oracle.simulate(n, specs, x=9), 0)
     s.free()
-    # unitary circuit: no promotion, stays complex64
+    # unitary circuit: no promotion, stays complex64; a basis start has norm exactly 1
     psi2, rep2 = run_gpu(sv, n, sv.gates_from_specs(specs), 0, 3, x=9, adaptive=True)
     assert rep2["promotions"] == 0 and rep2["dtype_used"] == 0 and rep2["drift"] < 1e-6
+    assert rep2["norm_before"] == 1.0
     check(psi2, oracle.simulate(n, specs, x=9), 0)
 
 
