@@ -685,7 +685,7 @@ def time_config(sv, torch, n, dtype, k, circuits, warmup, cycles=24):
             "state_bytes": (8 if dtype == sv.SV_C64 else 16) << n, "clocks": clk.summary()}
 
 
-def run_shard(args):
+def run_shard(args, emulate=None, steps=None, warmup=None, quiet=False):
     """One state over all ranks (global-qubit sharding): --n qubits per GPU, so n + g qubits
     on 2^g ranks (weak scaling: the amplitudes per GPU are fixed).  One step = sv_fuse
     (host) + the plan + every segment's passes and every exchange + the FP64 norm (one sum
@@ -699,7 +699,11 @@ def run_shard(args):
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
     dt = sv.SV_C64 if args.dtype == "c64" else sv.SV_C128
-    emulate = args.emulate_ranks if world == 1 else 0
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    if emulate is None:
+        emulate = args.emulate_ranks
+    emulate = emulate if world == 1 else 0
     ranks = emulate if emulate else world
     g = ranks.bit_length() - 1
     if (1 << g) != ranks:
@@ -719,20 +723,20 @@ def run_shard(args):
                 st.set_basis(0)
                 rep = st.apply_circuit(c)
                 return rep, st.norm(), st.topk(64)
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 step()
             torch.cuda.synchronize()
             comm.sum(0.0)                                   # all ranks start together
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             bytes0 = st.exchanged_bytes
-            for _ in range(args.steps):
+            for _ in range(steps):
                 rep, norm, top = step()
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             result[r] = {"ms": comm.allgather(ms), "rep": rep, "norm": norm,
-                         "exchanged_bytes_per_step": (st.exchanged_bytes - bytes0) / args.steps}
+                         "exchanged_bytes_per_step": (st.exchanged_bytes - bytes0) / steps}
             shard.free()
 
     result = {}
@@ -779,11 +783,11 @@ def run_shard(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     if rank != 0:
-        return
-    value = args.steps / (ms / 1000.0)
+        return None
+    value = steps / (ms / 1000.0)
     out = {"metric": "sharded circuits/s (one state over the ranks, global-qubit sharding)",
-           "value": value, "unit": "circuits/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "value": value, "unit": "circuits/s", "n_gpus": world, "steps": steps,
+           "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if dt == sv.SV_C64 else "f64", "data": "synthetic",
            "config": {"workload": f"grid_random {n_total}q depth {args.cycles}, {args.dtype}, "
@@ -795,13 +799,15 @@ def run_shard(args):
            "swap_passes_per_step": me["rep"]["swap_passes"],
            "exchanged_bytes_per_step_per_rank": me["exchanged_bytes_per_step"],
            "norm": me["norm"], "clocks": clk.summary()}
-    print(json.dumps(out), flush=True)
+    if not quiet:
+        print(json.dumps(out), flush=True)
+    return out
 
 
 def run_extras(args, sv, torch):
     """The rest of the headline metric, measured in the default run after the 30-qubit
     line: the grid circuits at 28 and 33 qubits (complex64) and at 30 and 32 qubits
-    (complex128, the width-5 schedule too), short batched and served summaries."""
+    (complex128, the width-5 schedule too), short batched, sharded and served summaries."""
     out = {}
     cfgs = [(28, sv.SV_C64, 5, 8, 2), (33, sv.SV_C64, 5, 3, 1), (30, sv.SV_C128, 4, 3, 1),
             (30, sv.SV_C128, 5, 2, 1), (32, sv.SV_C128, 4, 2, 1)]
@@ -815,6 +821,18 @@ def run_extras(args, sv, torch):
     torch.cuda.empty_cache()
     with ClockSampler(None) as clk:
         per_rate = serve_rates(sv, [10.0, 100.0], 100)
+    shard = {}
+    for ranks in (2, 4):
+        r = run_shard(args, emulate=ranks, steps=2, warmup=1, quiet=True)
+        shard[str(ranks)] = {kk: r[kk] for kk in ("value", "unit", "ms_per_step", "passes_per_step",
+                                                  "exchanges_per_step", "swap_passes_per_step",
+                                                  "exchanged_bytes_per_step_per_rank", "norm",
+                                                  "clocks")}
+    out["sharded"] = {"workload": f"grid_random {args.n}q depth {args.cycles}, {args.dtype}, k={args.k}, "
+                                  "one state over R ranks run as threads on this GPU (exchanges as "
+                                  "device copies; bench.py --mode shard under torchrun uses NCCL "
+                                  "between GPUs)", "per_ranks": shard}
+    torch.cuda.empty_cache()
     out["serving"] = {"workload": "serving_stream: Poisson arrivals, width U{10..30}, depth "
                                   "U{10..60}, 70% c64 / 30% c128, top-64, 150 GiB budget, 16 slots, "
                                   "fusion k = 4; 100 arrivals per rate (bench.py --mode serve "
