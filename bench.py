@@ -44,14 +44,14 @@ KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
             "sha256_prefix": "2c8c524322c9a611", "n": 30,
             "bytes_per_launch": (1.073810e9 + 1.014305e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 82.6% of GPU time, all apply kernels "
-                      "97.1% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 83.2% of GPU time, all apply kernels "
+                      "97.5% (profiles/fused_pass_grid30q_k5_launches.md)",
             "traffic_source": "apply_tc<5,0,2> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
              "sha256_prefix": "7184257e2a53bb42", "n": 30,
              "bytes_per_launch": (2.147548e9 + 2.085445e9) * 8,
-             "kernel": "fused-gate passes: apply_tc64<*> 98.2% of GPU time "
+             "kernel": "fused-gate passes: apply_tc64<*> 98.1% of GPU time "
                        "(profiles/fused_pass_grid30q_c128_k4_launches.md); bound by the "
                        "integer ALU pipe, not HBM (profiles/apply_tc64_c128_27q_ncu.md)",
              "traffic_source": "apply_tc64<0,*> ncu capture at 27q scaled to 30q "
