@@ -45,13 +45,15 @@ def test_expect_noalloc_matches_oracle_and_sv_expect(gpu, dtype):
     psi = sv.sv_get_state(s).astype(np.complex128)        # the state as stored
     xs, zs, cs = _terms(n, rng)
     want = oracle.expect(psi, xs, zs, cs)
-    assert _close(sv.sv_expect(s, xs, zs, cs), want, dtype)
+    existing = sv.sv_expect(s, xs, zs, cs)                       # the allocating entry point
+    assert _close(existing, want, dtype)
     out = torch.empty(1, dtype=torch.float64, device="cuda")     # owned by the caller
     for _ in range(2):                                           # two calls in a row
         out.fill_(float("nan"))
         sv.sv_expect_noalloc(buf, n, dtype, xs, zs, cs, out, stream=stream)
         stream.synchronize()
         got = float(out.item())
+        assert _close(got, existing, dtype), (got, existing)
         assert _close(got, want, dtype), (got, want)
     # a different state and fewer terms through the same scratch array
     sv.sv_set_basis(s, 3)
@@ -61,6 +63,7 @@ def test_expect_noalloc_matches_oracle_and_sv_expect(gpu, dtype):
     sv.sv_expect_noalloc(buf, n, dtype, xs[:7], zs[:7], cs[:7], out, stream=stream)
     stream.synchronize()
     assert _close(float(out.item()), want2, dtype)
+    assert _close(float(out.item()), sv.sv_expect(s, xs[:7], zs[:7], cs[:7]), dtype)
     s.free()
 
 
