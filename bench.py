@@ -5,8 +5,11 @@ Workload (default): 30 qubits on a 5 x 6 grid, 24 cycles of {sqrtX, sqrtY, sqrtW
 every qubit + fSim(pi/2, pi/6) on one of four edge classes (720 + 294 = 1014 gates),
 seeded; complex64 state (8 GiB, larger than L2), DAG fusion at k = 5, adaptive
 c64 -> c128 promotion on norm drift > 1e-6.  One step is the whole hot path:
-  sv_fuse (host DAG fusion) -> sv_set_basis -> sv_apply_circuit (FP64 norm before and
-  after, every fused pass) -> sv_topk(64) -> sv_expect(<Z0 Z1>).
+  sv_fuse (host DAG fusion) -> sv_set_basis -> sv_apply_circuit (every fused pass, then
+  the FP64 norm; a basis start's norm is exactly 1) -> sv_topk(64) -> sv_expect(<Z0 Z1>).
+The default run then adds the unfused complex128 comparison and the other configurations
+of the metric (28/33-qubit complex64, 30/32-qubit complex128, batched, sharded and served
+summaries) as extra keys of the same line.
 Metric: circuits/s (whole job), with the fused-gate HBM GB/s of the apply kernels.
 
 --impl reference times the CPU oracle (complex128, unfused, OpenMP over the host cores)
