@@ -470,7 +470,9 @@ sv_status sv_expect_noalloc(const void *psi, uint32_t n, sv_dtype dtype, const u
  * (exchanges, then SWAP passes inside the shards), so the shards again hold the amplitudes
  * in index order; a norm or a Pauli expectation without X/Y on the top g qubits is then
  * the sum over ranks of the shard's value, with the coefficient's sign from the Z part on
- * the top qubits, (-1)^popcount(zmask >> L & r).  complex128 plans use the circuit's
+ * the top qubits, (-1)^popcount(zmask >> L & r) (a term with X/Y on top qubits is summed
+ * after the same kind of exchange has swapped those qubits into local positions the
+ * term does not flip, and swapped back after).  complex128 plans use the circuit's
  * width-4 schedule when it has width-5 gates.  Host only; the transport (NCCL, or a copy
  * between processes) is the caller's. */
 #define SV_SHARD_APPLY 0u

@@ -213,19 +213,61 @@ class ShardedState:
     def norm(self) -> float:
         return self.comm.sum(self.local.norm())
 
-    def expect(self, xmask: Sequence[int], zmask: Sequence[int], coef: Sequence[float]) -> float:
-        """sum_t coef[t] <P_t>; X/Y parts must be on the low L qubits (Z anywhere)."""
+    def _local_terms(self, terms):
+        """Terms with no X/Y on the top qubits as this rank's terms: Z on a top qubit
+        contributes the sign of the rank's bit there."""
         lo = (1 << self.L) - 1
         xs, zs, cs = [], [], []
-        for x, z, c in zip(xmask, zmask, coef):
-            if x >> self.L:
-                raise ValueError("a Pauli term with X or Y on one of the top g qubits spans ranks; "
-                                 "only Z is allowed there")
+        for x, z, c in terms:
             sign = -1.0 if bin((z >> self.L) & self.rank).count("1") & 1 else 1.0
             xs.append(x)
             zs.append(z & lo)
             cs.append(sign * c)
-        return self.comm.sum(self.local.expect(xs, zs, cs))
+        return xs, zs, cs
+
+    def expect(self, xmask: Sequence[int], zmask: Sequence[int], coef: Sequence[float]) -> float:
+        """sum_t coef[t] <P_t> for Pauli strings on any qubits.  Terms are grouped by their
+        X/Y part on the top qubits; a group that flips top qubits has each of them swapped
+        into a local position the group does not flip (one exchange each, as in a plan),
+        is summed on the shards with its masks relabelled, and the same exchanges swap the
+        qubits back.  One FP64 sum over the ranks at the end."""
+        L = self.L
+        lo = (1 << L) - 1
+        groups = {}
+        for x, z, c in zip(xmask, zmask, coef):
+            if (x | z) >> self.n:
+                raise ValueError("a Pauli mask names a qubit >= n")
+            groups.setdefault(x >> L, []).append((x, z, c))
+        total = 0.0
+        for gx in sorted(groups):
+            terms = groups[gx]
+            if gx == 0:
+                total += self.local.expect(*self._local_terms(terms))
+                continue
+            js = [j for j in range(self.g) if (gx >> j) & 1]
+            flipped = 0
+            for x, _, _ in terms:
+                flipped |= x & lo
+            free = [p for p in range(L - 1, -1, -1) if not (flipped >> p) & 1]
+            if len(free) < len(js):
+                raise ValueError("too few local qubits outside the terms' X/Y part to swap the "
+                                 "top qubits in")
+            swaps = list(zip(free[:len(js)], js))
+            for p, j in swaps:
+                self._exchange(p, j)
+            mapped = []
+            for x, z, c in terms:
+                for p, j in swaps:                    # qubit L + j now at p, qubit p at L + j
+                    q = L + j
+                    bxq, bzq, bxp, bzp = (x >> q) & 1, (z >> q) & 1, (x >> p) & 1, (z >> p) & 1
+                    keep = ~((1 << q) | (1 << p))
+                    x = (x & keep) | (bxq << p) | (bxp << q)
+                    z = (z & keep) | (bzq << p) | (bzp << q)
+                mapped.append((x, z, c))
+            total += self.local.expect(*self._local_terms(mapped))
+            for p, j in reversed(swaps):
+                self._exchange(p, j)
+        return self.comm.sum(total)
 
     def topk(self, k: int) -> Tuple[np.ndarray, np.ndarray]:
         """The k most probable outcomes over all ranks, ties to the lower index."""

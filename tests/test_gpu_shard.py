@@ -62,7 +62,9 @@ def _run_sharded(sv, world, n, dtype, k, chunk, x, specs):
     out = [None] * world
     errors = []
     xs, zs, cs = W.zz_chain(n)
-    terms = (list(xs) + [0, 0b11], list(zs) + [(1 << (n - 1)) | 1, 0b10], list(cs) + [0.5, -0.25])
+    top, top2 = 1 << (n - 1), 1 << (n - 2)
+    terms = (list(xs) + [0, 0b11, top, top | top2 | 1], list(zs) + [top | 1, 0b10, top2, top | 0b110],
+             list(cs) + [0.5, -0.25, 0.8, -0.6])   # Z and X/Y on the top qubits too
 
     def worker(r):
         try:

@@ -8,8 +8,8 @@ reductions, against the oracle.
 * The executor (paper_2604_03816_gb300.shard.ShardedState) runs on 2 and 4 gloo ranks
   (processes) with TorchComm; each rank's local part is the oracle applied to its shard
   (test infrastructure standing in for a GPU).  The gathered state, norm, Pauli
-  expectations (ZZ chain, Z on the top qubits, X/Y on local ones) and top-k must equal the
-  oracle's on the whole state.
+  expectations (ZZ chain, Z on the top qubits, X/Y on local and on top qubits) and top-k
+  must equal the oracle's on the whole state.
 """
 import os
 import socket
@@ -138,18 +138,26 @@ def _rank_main(rank, world, port, n, k, out_dir):
         st = ShardedState(n, 1, comm, OracleShard(sv, L, chunk=16))
         st.set_basis(37)
         rep = st.apply_circuit(c)
-        xs, zs, cs = W.zz_chain(n)
-        top = (1 << (n - 1)) | (1 << (n - 2))
-        terms = (list(xs) + [0, 0, 0b101],
-                 list(zs) + [top, 1 << (n - 1), 0b110],
-                 list(cs) + [0.5, -1.25, 0.75])
+        terms = _terms(n)
         res = {"state": st.get_state(), "norm": st.norm(), "expect": st.expect(*terms),
                "topk": st.topk(10), "rep": rep, "bytes": st.exchanged_bytes}
+        # the layout is back to the identity after the swaps of the expectation
+        res["state_after"] = st.get_state()
         with pytest.raises(ValueError):
-            st.expect([1 << (n - 1)], [0], [1.0])      # X on a global qubit
+            st.expect([1 << n], [0], [1.0])            # qubit >= n
         np.save(os.path.join(out_dir, f"rank{rank}.npy"), np.array([res], dtype=object))
     finally:
         dist.destroy_process_group()
+
+
+def _terms(n):
+    """ZZ chain, Z on the top qubits, X/Y on local and on top qubits (one and two of
+    them, with Z and Y mixed in)."""
+    xs, zs, cs = W.zz_chain(n)
+    top, top2 = 1 << (n - 1), 1 << (n - 2)
+    return (list(xs) + [0, 0, 0b101, top, top | 0b10, top | top2, top2 | 1],
+            list(zs) + [top | top2, top, 0b110, 0, top | 0b1, top2 | 0b100, top2 | top],
+            list(cs) + [0.5, -1.25, 0.75, 0.3, -0.7, 1.1, 0.45])
 
 
 def _free_port():
@@ -169,13 +177,11 @@ def test_executor_on_gloo_ranks_matches_the_oracle(svlib, world, n, k):
         res = [np.load(os.path.join(d, f"rank{r}.npy"), allow_pickle=True)[0] for r in range(world)]
     specs = W.grid_random(n, 6) + W.random_unitary_gates(n, 12, 2, np.random.default_rng(7))
     ref = oracle.simulate(n, specs, x=37)
-    xs, zs, cs = W.zz_chain(n)
-    top = (1 << (n - 1)) | (1 << (n - 2))
-    want_e = oracle.expect(ref, list(xs) + [0, 0, 0b101], list(zs) + [top, 1 << (n - 1), 0b110],
-                           list(cs) + [0.5, -1.25, 0.75])
+    want_e = oracle.expect(ref, *_terms(n))
     want_i, want_p = oracle.topk(oracle.probs(ref), 10)
     for r in res:
         assert np.max(np.abs(r["state"] - ref)) < 1e-12
+        assert np.max(np.abs(r["state_after"] - ref)) < 1e-12
         assert abs(r["norm"] - 1.0) < 1e-12
         assert abs(r["expect"] - want_e) < 1e-12
         assert np.array_equal(r["topk"][0], want_i)
