@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-states", type=int, default=2,
+                    help="states in flight in the end-to-end loop (one host thread and stream each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare-unfused", action="store_true",
                     help="skip timing the unfused complex128 per-gate form of the circuit")
@@ -457,7 +459,7 @@ def run_qft(args):
     print(json.dumps(out), flush=True)
 
 
-def serve_rates(sv, rates, n_requests, budget_gib=150, slots=16, max_k=4):
+def serve_rates(sv, rates, n_requests, budget_gib=150, slots=16, max_k=5):
     """Poisson arrivals of seeded brickwork circuits (width U{10..30}, depth U{10..60}, 70%
     complex64 / 30% complex128, top-64 outcomes) at each offered rate, n_requests arrivals
     per rate (an arrival window of n_requests / rate seconds), through one server per rate
@@ -511,7 +513,8 @@ def run_serve(args):
            "steps": len(per_rate), "warmup": 0, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "mixed f32/f64", "data": "synthetic",
            "config": {"workload": "serving_stream", "budget_gib": 150, "max_slots": 16,
-                      "max_k": 4, "requests_per_rate": args.requests},
+                      "max_k": "5 (complex128 requests of 11+ qubits fused at 4)",
+                      "requests_per_rate": args.requests},
            "per_rate": per_rate, "clocks": clk.summary()}
     print(json.dumps(out), flush=True)
 
@@ -838,8 +841,8 @@ def run_extras(args, sv, torch):
     torch.cuda.empty_cache()
     out["serving"] = {"workload": "serving_stream: Poisson arrivals, width U{10..30}, depth "
                                   "U{10..60}, 70% c64 / 30% c128, top-64, 150 GiB budget, 16 slots, "
-                                  "fusion k = 4; 100 arrivals per rate (bench.py --mode serve "
-                                  "runs 500 per rate over six rates)",
+                                  "fusion k = 5 (complex128 at 4); 100 arrivals per rate "
+                                  "(bench.py --mode serve runs 500 per rate)",
                       "per_rate": per_rate, "clocks": clk.summary()}
     return out
 
@@ -942,72 +945,75 @@ def main():
             sv.sv_set_dtype(state, dt)
         # end to end through the C ABI with host buffers: every step copies the initial
         # state in from pinned host memory, fuses its circuit, applies it and writes all 2^n
-        # probabilities out to pinned host memory.  Two states with their own streams are
-        # driven by two host threads (double buffering, as a pipelined simulator would run),
-        # so one circuit's link transfers overlap the other's passes; the timed region is
-        # bracketed by CUDA events joined across both streams.
+        # probabilities out to pinned host memory.  --e2e-states states with their own
+        # streams are driven by as many host threads (pipelining, as a simulator serving a
+        # stream of circuits would run), so one circuit's link transfers overlap another's
+        # passes; the timed region is bracketed by CUDA events joined across the streams.
         e2e = None
         if args.e2e_steps > 0:
             npdt = np.complex64 if dt == sv.SV_C64 else np.complex128
             h_in = torch.zeros(1 << args.n, dtype=torch.complex64 if dt == sv.SV_C64
                                else torch.complex128).pin_memory()
             h_in[0] = 1.0
+            S = max(1, args.e2e_states)
             h_outs = [torch.empty(1 << args.n, dtype=torch.float32 if dt == sv.SV_C64
-                                  else torch.float64).pin_memory() for _ in range(2)]
+                                  else torch.float64).pin_memory() for _ in range(S)]
             h_in_np = h_in.numpy()
             assert h_in_np.dtype == npdt
-            streams = [stream, torch.cuda.Stream()]
-            states = [state, sv.sv_alloc(args.n, dt, stream=streams[1])]
+            streams = [stream] + [torch.cuda.Stream() for _ in range(S - 1)]
+            states = [state] + [sv.sv_alloc(args.n, dt, stream=streams[w]) for w in range(1, S)]
             # probabilities leave through a device buffer and the copy engine, so that one
-            # state's transfer does not hold the SMs while the other's passes run
+            # state's transfer does not hold the SMs while another's passes run
             for st_, ho in zip(states, h_outs):
                 sv.sv_set_policy(st_, sv.SV_POLICY_STAGED_PROBS)
                 sv.sv_probs(st_, ho.numpy())      # allocates the staging buffer, untimed
             torch.cuda.synchronize()
 
             import threading
-            first_in = threading.Event()
+            input_in = [threading.Event() for _ in range(S)]
 
             def worker(w, nsteps):
                 st, out = states[w], h_outs[w].numpy()
-                # the second state starts once the first one's input is in: started
-                # together, the two would move in lockstep (both uploading, then both
-                # computing at half speed) and no transfer would overlap a pass
-                if w == 1:
-                    first_in.wait()
+                # state w starts once state w-1's first input is in: started together, the
+                # states would move in lockstep (all uploading, then all computing at a
+                # fraction of the speed) and no transfer would overlap a pass
+                if w > 0:
+                    input_in[w - 1].wait()
                 with torch.cuda.stream(streams[w]):
                     for _ in range(nsteps):
                         if sv.sv_info(st)[1] != dt:
                             sv.sv_set_dtype(st, dt)
                         sv.sv_set_state(st, h_in_np)
-                        if w == 0:
-                            first_in.set()
+                        input_in[w].set()
                         c = sv.sv_fuse(gates, args.n, args.k)
                         sv.sv_apply_circuit(st, c, adaptive=True)
                         sv.sv_probs(st, out)
-                first_in.set()
+                input_in[w].set()
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(streams[0])
-            streams[1].wait_event(f0)
-            share = [(args.e2e_steps + 1) // 2, args.e2e_steps // 2]
-            with concurrent.futures.ThreadPoolExecutor(max_workers=2) as pool:
-                for fut in [pool.submit(worker, w, share[w]) for w in range(2)]:
+            for w in range(1, S):
+                streams[w].wait_event(f0)
+            share = [args.e2e_steps // S + (1 if w < args.e2e_steps % S else 0) for w in range(S)]
+            with concurrent.futures.ThreadPoolExecutor(max_workers=S) as pool:
+                for fut in [pool.submit(worker, w, share[w]) for w in range(S)]:
                     fut.result()
-            done1 = torch.cuda.Event()
-            done1.record(streams[1])
-            streams[0].wait_event(done1)
+            for w in range(1, S):
+                done = torch.cuda.Event()
+                done.record(streams[w])
+                streams[0].wait_event(done)
             f1.record(streams[0])
             torch.cuda.synchronize()
             e2e_ms = f0.elapsed_time(f1)
             e2e = {"value": world * args.e2e_steps / (e2e_ms / 1000.0), "unit": "circuits/s",
                    "h2d_bytes_per_step": int(h_in_np.nbytes),
                    "d2h_bytes_per_step": int(h_outs[0].numpy().nbytes),
-                   "steps": args.e2e_steps,
+                   "steps": args.e2e_steps, "states_in_flight": S,
                    "includes": "sv_set_state(host pinned) + sv_fuse + sv_apply_circuit + "
                                "sv_probs(host pinned, staged through the copy engine) per step; "
-                               "two states in flight on two streams (host threads), transfers "
-                               "of one overlapping the other's passes"}
-            states[1].free()
+                               f"{S} states in flight on {S} streams (host threads), transfers "
+                               "of one overlapping the others' passes"}
+            for w in range(1, S):
+                states[w].free()
             del h_in, h_outs
 
         unfused = None

@@ -390,7 +390,7 @@ typedef struct {
     size_t budget_bytes;     /* HBM budget of admitted requests (0: 150 GiB) */
     uint32_t max_slots;      /* requests in flight on the GPU (0: 16; at most 256) */
     uint32_t topk;           /* outcomes per result, 1..64 (0: 64) */
-    uint32_t max_k;          /* fusion width 1..5 (0: 4); complex128 requests of 11 or more
+    uint32_t max_k;          /* fusion width 1..5 (0: 5); complex128 requests of 11 or more
                                 qubits are fused at min(max_k, 4), the widest gate of the
                                 complex128 tensor-core pass */
     uint32_t fuse_threads;   /* host threads that fuse submitted circuits (0: 4) */

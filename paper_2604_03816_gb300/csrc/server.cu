@@ -291,7 +291,7 @@ sv_status sv_server_create(const sv_server_config *cfg, sv_server **out) {
     if (!S->cfg.max_slots) S->cfg.max_slots = 16;
     if (S->cfg.max_slots > 256) S->cfg.max_slots = 256;
     if (!S->cfg.topk || S->cfg.topk > 64) S->cfg.topk = 64;
-    if (!S->cfg.max_k) S->cfg.max_k = 4;
+    if (!S->cfg.max_k) S->cfg.max_k = 5;
     if (S->cfg.max_k > SV_MAX_K) S->cfg.max_k = SV_MAX_K;
     if (!S->cfg.fuse_threads) S->cfg.fuse_threads = 4;
     S->t0 = clk::now();
