@@ -72,8 +72,8 @@ def parse():
     ap.add_argument("--cycles", type=int, default=24)
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--e2e-steps", type=int, default=8)
-    ap.add_argument("--e2e-states", type=int, default=2,
+    ap.add_argument("--e2e-steps", type=int, default=12)
+    ap.add_argument("--e2e-states", type=int, default=4,
                     help="states in flight in the end-to-end loop (one host thread and stream each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare-unfused", action="store_true",
