@@ -81,6 +81,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the extra lines of the default run (28-33 qubit configurations, "
                          "complex128, batched and served summaries)")
+    ap.add_argument("--two-gate-passes", action="store_true",
+                    help="apply pairs of dense gates that fit one tile in one pass "
+                         "(SV_POLICY_TWO_GATE_PASSES; off by default)")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--mode", default="single",
                     choices=["single", "batched", "serve", "sample", "noise", "qft", "shard"],
@@ -528,6 +531,7 @@ def config_dict(args, ngates, nfused):
             "l2": "state larger than L2 (inputs > 129 MB), no flush needed",
             "host_fusion": "one sv_fuse per step, of the next circuit, on a host thread "
                            "overlapping the current circuit's GPU work",
+            "two_gate_passes": bool(getattr(args, "two_gate_passes", False)),
             "seed": W.seed_for(3, args.n)}
 
 
@@ -682,6 +686,7 @@ def time_config(sv, torch, n, dtype, k, circuits, warmup, cycles=24):
             "dtype": "c64" if dtype == sv.SV_C64 else "c128", "max_k": k,
             "max_k_used": reps[-1]["max_k_used"], "gates": len(specs),
             "fused_gates": runs[-1][1], "passes_per_circuit": reps[-1]["passes"],
+            "paired_passes_per_circuit": reps[-1]["paired_passes"],
             "tensor_core_passes": reps[-1]["tc_passes"], "circuits": circuits,
             "ms_per_circuit": ms, "circuits_per_s": 1000.0 / ms,
             "apply_ms_per_circuit": apply_ms / circuits,
@@ -883,6 +888,8 @@ def main():
     gates = sv.gates_from_specs(specs)          # gate construction: once, host
     ga = sv.GateArray(gates)
     state = sv.sv_alloc(args.n, dt, stream=stream)
+    base_policy = sv.SV_POLICY_TWO_GATE_PASSES if args.two_gate_passes else 0
+    sv.sv_set_policy(state, base_policy)
     launches_per_step = [0]
     # Each step fuses one circuit on the host (Algorithm 2) and runs it on the GPU; the
     # fusion of the next circuit runs on a host thread while the GPU works on the current
@@ -965,7 +972,7 @@ def main():
             # probabilities leave through a device buffer and the copy engine, so that one
             # state's transfer does not hold the SMs while another's passes run
             for st_, ho in zip(states, h_outs):
-                sv.sv_set_policy(st_, sv.SV_POLICY_STAGED_PROBS)
+                sv.sv_set_policy(st_, sv.SV_POLICY_STAGED_PROBS | base_policy)
                 sv.sv_probs(st_, ho.numpy())      # allocates the staging buffer, untimed
             torch.cuda.synchronize()
 
@@ -1043,6 +1050,8 @@ def main():
            "dtype": "f32" if dt == sv.SV_C64 else "f64", "data": "synthetic",
            "config": config_dict(args, len(specs), nfused),
            "fused_gate_hbm_gbs": achieved,
+           "passes_per_circuit": reps[-1]["passes"],
+           "paired_passes_per_circuit": reps[-1]["paired_passes"],
            "promotions": sum(r["promotions"] for r in reps),
            "max_drift": max(r["drift"] for r in reps),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -157,6 +157,15 @@ sv_status sv_circuit_size(const sv_circuit *c, size_t *nfused, uint32_t *n);
 sv_status sv_circuit_gate(const sv_circuit *c, size_t i, uint32_t *k, uint32_t *targets,
                           double *u);
 
+/* The passes sv_apply_circuit enqueues for the circuit's schedule on a complex64 state of
+ * the circuit's width with these SV_POLICY_* flags (two-gate passes: see
+ * sv_apply_circuit).  Pass i applies gate first[i] of the schedule, then gate second[i]
+ * when second[i] >= 0, in the same pass.  first and second hold room for `cap` entries
+ * (the schedule's gate count always suffices); *npasses gets the pass count.
+ * SV_ERR_ARG if cap is too small.  Host only. */
+sv_status sv_plan_passes(const sv_circuit *c, uint32_t policy, uint32_t *first, int32_t *second,
+                         size_t cap, size_t *npasses);
+
 /* ------------------------------------------------------- precision (R) and apply (E) */
 
 /* A-priori rule of Eqs. 11-12: eps_round = g * 2^n * 1.19e-7; complex64 iff
@@ -174,7 +183,8 @@ typedef struct {
 typedef struct {
     int32_t dtype_used;         /* sv_dtype that produced the final state */
     uint32_t promotions;        /* 1 if the circuit was replayed in complex128 */
-    uint64_t passes;            /* gate passes enqueued (including a replay) */
+    uint64_t passes;            /* HBM passes enqueued (including a replay); a two-gate
+                                   pass counts once */
     double norm_before;         /* FP64 norms when adaptive (else 0); norm_before of a basis
                                    start is exactly 1 and takes no pass */
     double norm_after;
@@ -184,10 +194,23 @@ typedef struct {
     double apply_ms;            /* with opts->timing: CUDA-event time of all passes (ms) */
     uint64_t tc_passes;         /* passes that ran on the tensor-core kernels */
     uint32_t max_k_used;        /* widest gate of the schedule that produced the final state */
+    uint64_t paired_passes;     /* passes that applied two fused gates (SV_POLICY_TWO_GATE_PASSES) */
 } sv_apply_report;
 
 /* Apply every gate of the fused schedule, in order, one pass over the state each (Eq. 10:
  * the fused product equals the unfused one).  opts may be NULL (no adaptivity).
+ *
+ * Two-gate passes (opt-in, SV_POLICY_TWO_GATE_PASSES; complex64 with tensor cores
+ * allowed, states of at least 13 qubits): two dense gates of the schedule whose targets,
+ * with the low index bits, fit one tile of 2^12 amplitudes (index bits [0, L) plus their
+ * targets at or above L, L >= 5) are applied in one read-write pass of the state, the
+ * tile kept in shared memory between them.  The second gate of a pair may be taken from
+ * further on in the schedule when every gate it passes over acts on other qubits (such
+ * gates commute with it; Eq. 8's DAG has no path between them), so the product is the
+ * schedule's.  report->passes counts the HBM passes, report->paired_passes those that
+ * applied two gates.  A two-gate pass is bound by instruction issue, not HBM: on GB300 it
+ * takes 1.6-1.8x the time of a one-gate pass when the tile is contiguous and more when
+ * it is gathered from short segments, so it is off by default.
  *
  * Precision (Section 5.4).  complex64 states compute in FP32 (tensor-core passes on exact
  * 9-bit fixed-point slices with FP32-level error relative to each group's largest
@@ -300,6 +323,9 @@ sv_status sv_gate_structure(const sv_gate *g, uint32_t *kind, uint32_t *control_
  * one copy-engine transfer, instead of the kernel writing over the CPU-GPU link itself: the
  * transfer then occupies no SM, so passes of states on other streams run meanwhile. */
 #define SV_POLICY_STAGED_PROBS 4u
+/* Apply pairs of dense complex64 gates that fit one tile in one pass (two-gate passes; see
+ * sv_apply_circuit).  Off by default. */
+#define SV_POLICY_TWO_GATE_PASSES 8u
 sv_status sv_set_policy(sv_state *s, uint32_t flags);
 
 /* ------------------------------------------------------------ batched execution */

@@ -338,6 +338,15 @@ Gate widen_gate(const Gate &g, uint32_t n, uint32_t m) {
     return w;
 }
 
+// g as an m-qubit gate U (x) I on the sorted qubit set qs (which contains g's targets).
+Gate widen_gate_on(const Gate &g, const uint32_t *qs, uint32_t m) {
+    Gate w;
+    w.k = m;
+    for (uint32_t j = 0; j < m; ++j) w.t[j] = qs[j];
+    w.u = embed(g, qs, m);
+    return w;
+}
+
 // Replay a recorded plan on gates with the same qubit sets: Algorithm 2's decisions
 // depend only on the qubits, so this yields the schedule fuse_gates would produce, with
 // the same products computed in the same order.

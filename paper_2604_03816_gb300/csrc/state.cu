@@ -435,6 +435,28 @@ sv_status sv_circuit_gate(const sv_circuit *c, size_t i, uint32_t *k, uint32_t *
     return SV_OK;
 }
 
+static void plan_passes(const sv_state *s, const std::vector<Gate> &gates, size_t begin, size_t end,
+                        std::vector<int> *first, std::vector<int> *second);
+
+sv_status sv_plan_passes(const sv_circuit *c, uint32_t policy, uint32_t *first, int32_t *second,
+                         size_t cap, size_t *npasses) {
+    clear_error();
+    if (!c || !first || !second || !npasses) return set_error(SV_ERR_ARG, "sv_plan_passes: null argument");
+    sv_state tmp;                   // host description only: no device memory is touched
+    tmp.n = c->n;
+    tmp.dtype = SV_C64;
+    tmp.policy = policy;
+    std::vector<int> f, sc;
+    plan_passes(&tmp, c->gates, 0, c->gates.size(), &f, &sc);
+    *npasses = f.size();
+    if (cap < f.size()) return set_error(SV_ERR_ARG, "sv_plan_passes: cap below the pass count");
+    for (size_t i = 0; i < f.size(); ++i) {
+        first[i] = (uint32_t)f[i];
+        second[i] = sc[i];
+    }
+    return SV_OK;
+}
+
 sv_status sv_choose_dtype(uint32_t n, uint64_t g, double eps_tol, sv_dtype *out, double *eps_round) {
     clear_error();
     if (!out) return set_error(SV_ERR_ARG, "sv_choose_dtype: null out");
@@ -469,10 +491,73 @@ sv_status sv_apply_gate(sv_state *s, const sv_gate *g) {
     return launch_apply(s, sorted_gate(g->k, g->targets, g->u));
 }
 
-// Enqueue passes [begin, end).  With `timing`, CUDA events on the state's stream bracket
-// the passes and their elapsed time is added to *ms (this synchronises on the events).
+// With SV_POLICY_TWO_GATE_PASSES: would launch_apply run g as a dense pass (tensor cores,
+// or the CUDA cores for k <= 3) on this complex64 state, so that it may share a pass with
+// another dense gate?
+static bool pair_candidate(const sv_state *s, const Gate &g) {
+    if (s->dtype != SV_C64 || !(s->policy & SV_POLICY_TWO_GATE_PASSES) || (s->policy & SV_POLICY_NO_TENSOR_CORES))
+        return false;
+    if (!(s->policy & SV_POLICY_DENSE_ONLY) && struct_preferred(s, classify(g))) return false;
+    return true;
+}
+
+// The passes of gates [begin, end): each gate in schedule order starts a pass unless an
+// earlier pass took it; a dense complex64 gate takes as its partner the first later dense
+// gate (within a window of 64) whose predecessors in the DAG of Eq. 8 (the last earlier
+// gate on each of its qubits) have all been applied, and whose targets fit one tile with
+// its own.  The partner then commutes with every gate it passes over (they share no
+// qubit), so the product of the passes is the schedule's.  first[i]: the gate that
+// pass i starts with; second[i]: its partner or -1.
+static void plan_passes(const sv_state *s, const std::vector<Gate> &gates, size_t begin, size_t end,
+                        std::vector<int> *first, std::vector<int> *second) {
+    const size_t m = end - begin;
+    std::vector<char> cand(m), done(m, 0);
+    std::vector<int> preds;                    // up to SV_MAX_K per gate, -1 = none
+    preds.assign(m * SV_MAX_K, -1);
+    std::vector<int> last(64, -1);
+    bool any = false;
+    for (size_t i = 0; i < m; ++i) {
+        const Gate &g = gates[begin + i];
+        cand[i] = pair_candidate(s, g);
+        any = any || cand[i];
+        for (uint32_t j = 0; j < g.k; ++j) {
+            preds[i * SV_MAX_K + j] = last[g.t[j]];
+            last[g.t[j]] = (int)i;
+        }
+    }
+    first->clear();
+    second->clear();
+    const size_t window = 64;
+    for (size_t i = 0; i < m; ++i) {
+        if (done[i]) continue;
+        done[i] = 1;
+        int partner = -1;
+        if (any && cand[i]) {
+            for (size_t v = i + 1; v < m && v <= i + window; ++v) {
+                if (done[v] || !cand[v]) continue;
+                bool ready = true;
+                for (uint32_t j = 0; j < SV_MAX_K && ready; ++j) {
+                    const int p = preds[v * SV_MAX_K + j];
+                    ready = p < 0 || done[p];
+                }
+                if (!ready || !tc2_pair_fits(s, gates[begin + i], gates[begin + v])) continue;
+                partner = (int)v;
+                done[v] = 1;
+                break;
+            }
+        }
+        first->push_back((int)(begin + i));
+        second->push_back(partner < 0 ? -1 : (int)(begin + partner));
+    }
+}
+
+// Enqueue the passes of gates [begin, end).  With `timing`, CUDA events on the state's
+// stream bracket the passes and their elapsed time is added to *ms (this synchronises on
+// the events).
 static sv_status run_schedule(sv_state *s, const std::vector<Gate> &gates, size_t begin, size_t end,
                               bool timing, sv_apply_report *r) {
+    std::vector<int> first, second;
+    plan_passes(s, gates, begin, end, &first, &second);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timing) {
         SV_CUDA(cudaEventCreate(&e0));
@@ -480,15 +565,25 @@ static sv_status run_schedule(sv_state *s, const std::vector<Gate> &gates, size_
         SV_CUDA(cudaEventRecord(e0, s->stream));
     }
     sv_status st = SV_OK;
-    for (size_t i = begin; i < end && st == SV_OK; ++i) {
+    for (size_t i = 0; i < first.size() && st == SV_OK; ++i) {
+        const Gate &g = gates[first[i]];
+        if (second[i] >= 0) {
+            const Gate &g2 = gates[second[i]];
+            st = launch_apply_tc2(s, g, g2);
+            r->bytes += 2ull * (8ull << s->n);
+            ++r->tc_passes;
+            ++r->paired_passes;
+            r->max_k_used = std::max(r->max_k_used, std::max(g.k, g2.k));
+            continue;
+        }
         uint64_t b = 0;
         int kind = PASS_CUDA_CORE;
-        st = launch_apply(s, gates[i], &b, &kind);
+        st = launch_apply(s, g, &b, &kind);
         r->bytes += b;
         if (kind == PASS_TENSOR_CORE) ++r->tc_passes;
-        r->max_k_used = std::max(r->max_k_used, gates[i].k);
+        r->max_k_used = std::max(r->max_k_used, g.k);
     }
-    r->passes += end - begin;
+    r->passes += first.size();
     if (timing) {
         cudaError_t e = cudaEventRecord(e1, s->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -718,7 +813,8 @@ sv_status sv_debug_fail_allocs(uint32_t count) {
 sv_status sv_set_policy(sv_state *s, uint32_t flags) {
     clear_error();
     if (!s) return set_error(SV_ERR_ARG, "sv_set_policy: null state");
-    if (flags & ~(SV_POLICY_NO_TENSOR_CORES | SV_POLICY_DENSE_ONLY | SV_POLICY_STAGED_PROBS))
+    if (flags & ~(SV_POLICY_NO_TENSOR_CORES | SV_POLICY_DENSE_ONLY | SV_POLICY_STAGED_PROBS |
+                  SV_POLICY_TWO_GATE_PASSES))
         return set_error(SV_ERR_ARG, "sv_set_policy: unknown flag");
     s->policy = flags;
     return SV_OK;

@@ -55,6 +55,8 @@ std::vector<Gate> fuse_gates(const std::vector<Gate> &in, uint32_t n, uint32_t m
 uint32_t diagonal_mask(const Gate &g);
 // g as an m-qubit gate U (x) I (m >= g.k, m <= n; fuse.cpp).
 Gate widen_gate(const Gate &g, uint32_t n, uint32_t m);
+// g as an m-qubit gate U (x) I on the sorted qubits qs (containing g's targets).
+Gate widen_gate_on(const Gate &g, const uint32_t *qs, uint32_t m);
 // Apply a recorded plan to gates with the same qubit sets (fuse.cpp).
 std::vector<Gate> replay_fusion(std::vector<Gate> nodes, const FusePlan &plan);
 
@@ -150,6 +152,10 @@ bool tc_eligible(const sv_state *s, const Gate &g);        // apply_tc.cu
 sv_status launch_apply_tc(sv_state *s, const Gate &g);
 bool tc64_eligible(const sv_state *s, const Gate &g);      // apply_tc64.cu
 sv_status launch_apply_tc64(sv_state *s, const Gate &g);
+// Two complex64 gates in one pass (apply_tc2.cu): do they fit one tile, and run them
+// (g0 first).
+bool tc2_pair_fits(const sv_state *s, const Gate &g0, const Gate &g1);
+sv_status launch_apply_tc2(sv_state *s, const Gate &g0, const Gate &g1);
 sv_status launch_norm(sv_state *s, double *dev_out);     // writes one double on device
 sv_status launch_probs(sv_state *s, void *dev_out);
 sv_status launch_density_probs(sv_state *s, void *dev_out);   // Re v[x + 2^(n/2) x]

@@ -34,7 +34,7 @@ EXPORTS = ["sv_gate_matrix", "sv_alloc", "sv_free", "sv_info", "sv_set_basis", "
            "sv_get_state", "sv_fuse", "sv_circuit_free", "sv_circuit_size", "sv_circuit_gate",
            "sv_choose_dtype", "sv_apply_circuit", "sv_apply_gate", "sv_norm", "sv_probs",
            "sv_expect", "sv_topk", "sv_sync", "sv_last_error", "sv_set_policy",
-           "sv_expect_noalloc"]
+           "sv_expect_noalloc", "sv_plan_passes"]
 EXPORTS += ["sv_fuse_like", "sv_sample", "sv_fuse_density", "sv_density_probs", "sv_gate_structure",
             "sv_fuse_ex", "sv_debug_fail_allocs", "sv_set_zero", "sv_shard_plan_create",
             "sv_shard_plan_free", "sv_shard_plan_info", "sv_shard_plan_step", "sv_shard_pack",
@@ -46,6 +46,7 @@ EXPORTS += ["sv_batch_alloc", "sv_batch_free", "sv_batch_set_basis", "sv_batch_g
 SV_POLICY_NO_TENSOR_CORES = 1
 SV_POLICY_DENSE_ONLY = 2
 SV_POLICY_STAGED_PROBS = 4
+SV_POLICY_TWO_GATE_PASSES = 8
 SV_FUSE_COMMUTE = 1
 SV_STRUCT_DENSE, SV_STRUCT_DIAGONAL, SV_STRUCT_MONOMIAL, SV_STRUCT_IDENTITY = 0, 1, 2, 3
 SV_SHARD_APPLY, SV_SHARD_SWAP = 0, 1
@@ -72,7 +73,8 @@ class sv_apply_report(ctypes.Structure):
                 ("passes", ctypes.c_uint64), ("norm_before", ctypes.c_double),
                 ("norm_after", ctypes.c_double), ("drift", ctypes.c_double),
                 ("bytes", ctypes.c_uint64), ("apply_ms", ctypes.c_double),
-                ("tc_passes", ctypes.c_uint64), ("max_k_used", ctypes.c_uint32)]
+                ("tc_passes", ctypes.c_uint64), ("max_k_used", ctypes.c_uint32),
+                ("paired_passes", ctypes.c_uint64)]
 
 
 class sv_batch_opts(ctypes.Structure):
@@ -174,6 +176,8 @@ _sig = {
     "sv_batch_sync": [_vp],
     "sv_batch_tune": [_vp, ctypes.POINTER(sv_gate), ctypes.c_size_t, _u32, _u32,
                       ctypes.POINTER(sv_tune_result)],
+    "sv_plan_passes": [_vp, _u32, ctypes.POINTER(_u32), ctypes.POINTER(ctypes.c_int32), ctypes.c_size_t,
+                       ctypes.POINTER(ctypes.c_size_t)],
     "sv_expect_noalloc": [_vp, _u32, _i32, ctypes.POINTER(_u64), ctypes.POINTER(_u64), _dp,
                           ctypes.c_size_t, _vp, _vp],
 }
@@ -315,6 +319,17 @@ def sv_circuit_gate(c: Circuit, i: int) -> Tuple[Tuple[int, ...], np.ndarray]:
     return tuple(int(tg[j]) for j in range(k.value)), u.view(np.complex128).reshape(d, d)
 
 
+def sv_plan_passes(c: Circuit, policy: int = SV_POLICY_TWO_GATE_PASSES) -> List[Tuple[int, int]]:
+    """The passes of the circuit on a complex64 state with these policy flags:
+    [(first, second or -1)]."""
+    nf, _ = sv_circuit_size(c)
+    first = (_u32 * max(nf, 1))()
+    second = (ctypes.c_int32 * max(nf, 1))()
+    np_ = ctypes.c_size_t()
+    _check(_lib.sv_plan_passes(c.handle, policy, first, second, max(nf, 1), ctypes.byref(np_)))
+    return [(int(first[i]), int(second[i])) for i in range(np_.value)]
+
+
 def sv_choose_dtype(n: int, g: int, eps_tol: float) -> Tuple[int, float]:
     out, e = _i32(), ctypes.c_double()
     _check(_lib.sv_choose_dtype(n, g, eps_tol, ctypes.byref(out), ctypes.byref(e)))
@@ -420,7 +435,7 @@ def sv_apply_circuit(s: State, c: Circuit, adaptive: bool = False, drift_thresho
     return {"dtype_used": rep.dtype_used, "promotions": rep.promotions, "passes": rep.passes,
             "norm_before": rep.norm_before, "norm_after": rep.norm_after, "drift": rep.drift,
             "bytes": rep.bytes, "apply_ms": rep.apply_ms, "tc_passes": rep.tc_passes,
-            "max_k_used": rep.max_k_used}
+            "max_k_used": rep.max_k_used, "paired_passes": rep.paired_passes}
 
 
 def sv_apply_gate(s: State, targets: Sequence[int], u: np.ndarray) -> None:

@@ -103,7 +103,7 @@ def test_grid_random_full_size_tensor_vs_cuda_cores(gpu, n, dtype, k):
         s = sv.sv_alloc(n, dtype, dev_buf=buf, stream=torch.cuda.current_stream())
         sv.sv_set_policy(s, policy)
         rep = sv.sv_apply_circuit(s, c)
-        assert rep["passes"] == len(c)
+        assert rep["passes"] + rep["paired_passes"] == len(c)
         if policy == 0:
             assert rep["tc_passes"] >= 0.75 * rep["passes"]
         else:

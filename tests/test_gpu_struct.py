@@ -152,7 +152,9 @@ def test_qft_circuit_structure_vs_dense(gpu, dtype, k):
         psi = sv.sv_get_state(s).astype(np.complex128)
         s.free()
         assert float(np.max(np.abs(psi - ref))) <= TOL[dtype]
-    assert reps[0]["passes"] == reps[sv.SV_POLICY_DENSE_ONLY]["passes"]
+    # every fused gate is applied once either way (dense gates may share a pass)
+    assert (reps[0]["passes"] + reps[0]["paired_passes"] ==
+            reps[sv.SV_POLICY_DENSE_ONLY]["passes"] + reps[sv.SV_POLICY_DENSE_ONLY]["paired_passes"])
     assert reps[0]["bytes"] < 0.8 * reps[sv.SV_POLICY_DENSE_ONLY]["bytes"]
 
 

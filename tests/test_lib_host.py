@@ -263,3 +263,79 @@ def test_new_entry_points_validate_arguments(svlib):
     ga = svlib.GateArray([((0, 1), OG.matrix("cz"))])
     kind = ctypes.c_uint32()
     assert lib.sv_gate_structure(ga.arr, ctypes.byref(kind), None) == 0 and kind.value == svlib.SV_STRUCT_DIAGONAL
+
+
+def _tile_low_bits(u):
+    """Largest L with L + #{targets >= L} <= 12 (the two-gate pass's tile of 2^12)."""
+    for L in range(12, -1, -1):
+        if L + sum(1 for t in u if t >= L) <= 12:
+            return L
+    return -1
+
+
+@pytest.mark.parametrize("case", ["grid14", "random15", "qft_brickwork13", "random16_k3"])
+def test_pass_plan_pairs_commuting_gates_within_one_tile(svlib, case):
+    """The two-gate pass plan (sv_plan_passes, SV_POLICY_TWO_GATE_PASSES): every gate once; each pair fits one
+    2^12-amplitude tile with segments of at least 2^5 amplitudes; two gates that share a
+    qubit keep their schedule order (so only commuting gates are reordered, Eq. 8's DAG);
+    only dense gates without controls are paired; and the oracle's state after the gates in
+    plan order equals its state after the schedule."""
+    sv = svlib
+    rng = np.random.default_rng(4242)
+    if case == "grid14":
+        n, specs = 14, W.grid_random(14, 8)
+    elif case == "random15":
+        n, specs = 15, W.random_unitary_gates(15, 60, 5, rng)
+    elif case == "qft_brickwork13":
+        n, (_, specs) = 13, W.qft_brickwork(13, 6)
+    else:
+        n, specs = 16, W.random_unitary_gates(16, 80, 3, rng)
+    c = sv.sv_fuse(sv.gates_from_specs(specs), n, 5 if case != "random16_k3" else 3)
+    nf, _ = sv.sv_circuit_size(c)
+    gates = [sv.sv_circuit_gate(c, i) for i in range(nf)]
+    plan = sv.sv_plan_passes(c)
+    order = [g for a, b in plan for g in ((a,) if b < 0 else (a, b))]
+    assert sorted(order) == list(range(nf))
+    pairs = [(a, b) for a, b in plan if b >= 0]
+    assert len(pairs) >= 1
+    for a, b in pairs:
+        assert _tile_low_bits(set(gates[a][0]) | set(gates[b][0])) >= 5
+        for g in (a, b):
+            kind, ctrl = sv.sv_gate_structure(gates[g][0], gates[g][1])
+            assert kind == sv.SV_STRUCT_DENSE and ctrl == 0
+    pos = {g: i for i, g in enumerate(order)}
+    for i in range(nf):
+        for j in range(i + 1, nf):
+            if set(gates[i][0]) & set(gates[j][0]):
+                assert pos[i] < pos[j], (i, j)
+    v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+    psi0 = v / np.linalg.norm(v)
+    ref = oracle.run(psi0, gates)
+    got = oracle.run(psi0, [gates[g] for g in order])
+    assert np.max(np.abs(got - ref)) <= 1e-12
+    # no pairs by default or without tensor cores; every dense gate is a candidate with DENSE_ONLY
+    P = sv.SV_POLICY_TWO_GATE_PASSES
+    assert sv.sv_plan_passes(c, 0) == [(i, -1) for i in range(nf)]
+    assert len(sv.sv_plan_passes(c, P | sv.SV_POLICY_DENSE_ONLY)) <= len(plan)
+    assert sv.sv_plan_passes(c, P | sv.SV_POLICY_NO_TENSOR_CORES) == [(i, -1) for i in range(nf)]
+
+
+def test_pass_plan_skips_only_gates_on_other_qubits(svlib):
+    """A pair partner is taken from further on only past gates on other qubits: g0 on
+    5..9 pairs with g2 on 5..8 and 15 (g1 on 10..14 shares no qubit with g2); when g1
+    also acts on qubit 15, g2 must wait and no pair forms; gates whose union needs more
+    than the tile's bits (L < 5) stay apart."""
+    sv = svlib
+    rng = np.random.default_rng(99)
+    n = 16
+
+    def plan(tsets):
+        specs = [W.GateSpec("unitary", t, (), False, W.haar_unitary(1 << len(t), rng)) for t in tsets]
+        c = sv.sv_fuse(sv.gates_from_specs(specs), n, 0)
+        return sv.sv_plan_passes(c)
+
+    assert plan([(5, 6, 7, 8, 9), (10, 11, 12, 13, 14), (5, 6, 7, 8, 15)]) == [(0, 2), (1, -1)]
+    assert plan([(5, 6, 7, 8, 9), (10, 11, 12, 13, 15), (5, 6, 7, 8, 15)]) == [(0, -1), (1, -1), (2, -1)]
+    assert plan([(5, 6, 7, 8, 9), (10, 11, 12, 13, 14)]) == [(0, -1), (1, -1)]
+    assert plan([(0, 1, 2, 3, 4), (0, 9, 13, 14, 15)]) == [(0, 1)]
+    assert plan([(3,), (7, 9)]) == [(0, 1)]
