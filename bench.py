@@ -86,13 +86,14 @@ def parse():
                          "(SV_POLICY_TWO_GATE_PASSES; off by default)")
     ap.add_argument("--cpu-sample-s", type=float, default=12.0)
     ap.add_argument("--mode", default="single",
-                    choices=["single", "batched", "serve", "sample", "noise", "qft", "shard"],
+                    choices=["single", "batched", "serve", "sample", "noise", "qft", "shard", "pairs"],
                     help="single: the 30-qubit hot path (default line); batched: 512 HEA "
                          "circuits of 16-22 qubits; serve: Poisson request stream; sample: "
                          "measurement shots from the 30-qubit circuit's output state; "
                          "qft: QFT of a basis state with structure-aware passes against "
                          "the same schedule forced dense; shard: one state over the "
-                         "ranks (global-qubit sharding, NCCL exchanges), --n qubits per GPU")
+                         "ranks (global-qubit sharding, NCCL exchanges), --n qubits per GPU; "
+                         "pairs: two-gate passes per tile layout against one-gate passes")
     ap.add_argument("--emulate-ranks", type=int, default=0,
                     help="shard: run this many ranks as threads on one GPU (exchanges are "
                          "device copies) instead of one process per GPU")
@@ -852,6 +853,55 @@ def run_extras(args, sv, torch):
     return out
 
 
+# Tile layouts of two-gate passes (SV_POLICY_TWO_GATE_PASSES), as pairs of target sets:
+# a contiguous tile, targets among the bank bits, and segments of 1 KiB, 512 B and 256 B.
+PAIR_LAYOUTS = [
+    ("contiguous L=12", (5, 6, 7, 8, 9), (7, 8, 9, 10, 11)),
+    ("bank targets L=12", (0, 1, 2, 6, 7), (2, 3, 4, 9, 10)),
+    ("1 KiB segments L=7", (16, 17, 22, 23), (4, 5, 11, 17)),
+    ("1 KiB segments, bank targets L=7", (3, 4, 5, 11, 17), (9, 10, 11, 16, 17)),
+    ("512 B segments L=6", (5, 11, 17, 23, 27), (4, 5, 10, 11, 16)),
+    ("256 B segments L=5", (21, 22, 26, 27), (19, 20, 21, 25, 26)),
+]
+
+
+def run_pairs(args):
+    """Two-gate passes per tile layout: 16 random unitaries alternating between the two
+    target sets of a layout, applied with SV_POLICY_TWO_GATE_PASSES (8 passes) and one gate
+    per pass (16 passes); the best of three timed runs (CUDA events on the state's
+    stream, after a warm-up).  The state (--n qubits, complex64) exceeds L2."""
+    import torch
+    from paper_2604_03816_gb300 import sv
+    torch.cuda.set_device(0)
+    n = args.n
+    rng = np.random.default_rng(W.seed_for(9, n))
+    stream = torch.cuda.Stream()
+    rows = []
+    with torch.cuda.stream(stream):
+        s = sv.sv_alloc(n, sv.SV_C64, stream=stream)
+        with ClockSampler(None) as clk:
+            for name, t0, t1 in PAIR_LAYOUTS:
+                specs = [W.GateSpec("unitary", t, (), False, W.haar_unitary(1 << len(t), rng))
+                         for t in (t0, t1) * 8]
+                c = sv.sv_fuse(sv.gates_from_specs(specs), n, 0)
+                row = {"layout": name, "targets": [list(t0), list(t1)]}
+                for pol, key in ((sv.SV_POLICY_TWO_GATE_PASSES, "two_gate"), (0, "one_gate")):
+                    sv.sv_set_policy(s, pol)
+                    sv.sv_set_basis(s, 3)
+                    sv.sv_apply_circuit(s, c)
+                    best, rep = 1e30, None
+                    for _ in range(3):
+                        rep = sv.sv_apply_circuit(s, c, timing=True)
+                        best = min(best, rep["apply_ms"])
+                    row[key + "_ms_per_pass"] = best / rep["passes"]
+                    row[key + "_passes"] = rep["passes"]
+                row["two_gate_over_two_one_gate"] = row["two_gate_ms_per_pass"] / (2 * row["one_gate_ms_per_pass"])
+                rows.append(row)
+        s.free()
+    print(json.dumps({"metric": "two-gate pass time per tile layout", "n_qubits": n, "dtype": "c64",
+                      "unit": "ms per pass", "layouts": rows, "clocks": clk.summary()}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -874,6 +924,9 @@ def main():
         return
     if args.mode == "shard":
         run_shard(args)
+        return
+    if args.mode == "pairs":
+        run_pairs(args)
         return
     rank, world, local = dist_info()
     import torch
