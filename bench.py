@@ -45,10 +45,10 @@ FALLBACK_HBM_GBS = 6800.0
 # as null once those sources hash differently).
 KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
-            "sha256_prefix": "2c8c524322c9a611", "n": 30,
-            "bytes_per_launch": (1.073810e9 + 1.014305e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 83.2% of GPU time, all apply kernels "
-                      "97.5% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "sha256_prefix": "88cf5e1b92fe0f5d", "n": 30,
+            "bytes_per_launch": (1.073862e9 + 1.012122e9) * 8,
+            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 82.9% of GPU time, all apply kernels "
+                      "97.6% (profiles/fused_pass_grid30q_k5_launches.md)",
             "traffic_source": "apply_tc<5,0,2> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),

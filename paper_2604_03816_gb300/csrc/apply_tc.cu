@@ -560,24 +560,38 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
                 const uint32_t gbase = gb[sub];
                 const float osc = row_scale[js & 3u][row];
                 const uint32_t lane_addr = tmem + b * S::ACC + ((quad * 32u) << 16) + part * HALF * 2u;
-                float2 o[HALF];
+                if constexpr (XP) {
+                    float2 o[HALF];
 #pragma unroll
-                for (uint32_t c0 = 0; c0 < 2u * HALF; c0 += 16) {
-                    float d0[16], d12[16];
-                    tmem_ld16(lane_addr + c0, d0);
-                    tmem_ld16(lane_addr + KD + c0, d12);
+                    for (uint32_t c0 = 0; c0 < 2u * HALF; c0 += 16) {
+                        float d0[16], d12[16];
+                        tmem_ld16(lane_addr + c0, d0);
+                        tmem_ld16(lane_addr + KD + c0, d12);
 #pragma unroll
-                    for (uint32_t i = 0; i < 16; i += 2) {
-                        const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
-                        const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
-                        o[(c0 + i) / 2] = make_float2(re, im);
+                        for (uint32_t i = 0; i < 16; i += 2) {
+                            const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
+                            const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
+                            o[(c0 + i) / 2] = make_float2(re, im);
+                        }
                     }
-                }
-                if constexpr (XP) xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < HALF)
+                    xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < HALF)
 #pragma unroll
-                for (uint32_t c = 0; c < HALF; ++c) {
-                    const uint32_t mo = member_off(part * HALF + c);
-                    out[gbase | (XP ? (mo ^ cx) : mo)] = o[c];
+                    for (uint32_t c = 0; c < HALF; ++c) out[gbase | (member_off(part * HALF + c) ^ cx)] = o[c];
+                } else {
+                    // member order: each chunk of eight members is written as soon as it is
+                    // formed (fewer live registers than holding the half row)
+#pragma unroll
+                    for (uint32_t c0 = 0; c0 < 2u * HALF; c0 += 16) {
+                        float d0[16], d12[16];
+                        tmem_ld16(lane_addr + c0, d0);
+                        tmem_ld16(lane_addr + KD + c0, d12);
+#pragma unroll
+                        for (uint32_t i = 0; i < 16; i += 2) {
+                            const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
+                            const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
+                            out[gbase | member_off(part * HALF + (c0 + i) / 2)] = make_float2(re, im);
+                        }
+                    }
                 }
                 tc_fence_before();
                 fence_proxy_async_smem();

@@ -339,3 +339,23 @@ def test_pass_plan_skips_only_gates_on_other_qubits(svlib):
     assert plan([(5, 6, 7, 8, 9), (10, 11, 12, 13, 14)]) == [(0, -1), (1, -1)]
     assert plan([(0, 1, 2, 3, 4), (0, 9, 13, 14, 15)]) == [(0, 1)]
     assert plan([(3,), (7, 9)]) == [(0, 1)]
+
+
+def test_plan_passes_validates_arguments(svlib):
+    """sv_plan_passes: null arguments and a too-small output capacity are reported (host)."""
+    import ctypes
+    lib = ctypes.CDLL(svlib.LIB_PATH)
+    rng = np.random.default_rng(5)
+    specs = W.random_unitary_gates(14, 6, 5, rng)
+    c = svlib.sv_fuse(svlib.gates_from_specs(specs), 14, 0)
+    first = (ctypes.c_uint32 * 6)()
+    second = (ctypes.c_int32 * 6)()
+    npasses = ctypes.c_size_t()
+    P = svlib.SV_POLICY_TWO_GATE_PASSES
+    assert lib.sv_plan_passes(None, P, first, second, 6, ctypes.byref(npasses)) != 0
+    assert lib.sv_plan_passes(ctypes.c_void_p(c.handle), P, None, second, 6, ctypes.byref(npasses)) != 0
+    assert lib.sv_plan_passes(ctypes.c_void_p(c.handle), P, first, second, 6, None) != 0
+    assert lib.sv_plan_passes(ctypes.c_void_p(c.handle), P, first, second, 0, ctypes.byref(npasses)) != 0
+    assert npasses.value >= 1                      # the count is reported even when cap is short
+    assert lib.sv_plan_passes(ctypes.c_void_p(c.handle), P, first, second, 6, ctypes.byref(npasses)) == 0
+    assert 1 <= npasses.value <= 6
