@@ -44,8 +44,10 @@
 // memory, shared memory holds only B, the raw stages and the output staging, so 4 (k = 5)
 // or 8 (k = 4) tiles of loads can be in flight per SM.  Every wait is bounded and any
 // role that gives up makes the others leave too (abort flag).
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -97,6 +99,10 @@ struct TcShape {
 
 template <int K>
 struct TcArgs {
+    // swizzled launches (SW): the state as a 2-D tensor of 128-byte rows (32 floats), boxes
+    // of box_rows rows, `boxes` boxes per segment, 128-byte swizzle in shared memory
+    CUtensorMap tmap;                      // 128-byte aligned by its type
+    uint32_t box_rows, boxes;
     int16_t b[3][(2u << K) * (2u << K)];   // slices of R (row-major n x kk), |b| <= 256
     float b_inv_scale;                     // R = (b1 + b2 2^-9 + b3 2^-18) * b_inv_scale
     void *psi;
@@ -223,7 +229,14 @@ __device__ __forceinline__ void b_grid(float m, float &sb, float &inv) {
 // contiguous range of tiles (so it meets few states), B is double-buffered and rebuilt by
 // the producer warp from the next state's matrix when its first tile comes up (b_full:
 // built; b_empty: the MMAs of the state that last used the set have completed).
-template <int K, bool XP, int SUB, bool BT = false>
+// SW: tiles move by 2-D tensor-map copies that store them in shared memory with the
+// 128-byte swizzle (16-byte chunk index XOR the 128-byte row within each 1 KiB), and the
+// roles address the tile through the same swizzle.  A warp's lanes (consecutive groups)
+// then reach different banks whatever the targets, so no lane-dependent member order is
+// needed (XP = false) and every layout takes two subtiles per stage.  The swizzle is linear
+// over XOR, so it is applied to the group base and to the target bits once, and member
+// offsets combine them by XOR.
+template <int K, bool XP, int SUB, bool BT = false, bool SW = false>
 __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArgs<K> a) {
     using S = TcShape<K, SUB, BT>;
     constexpr uint32_t KD = S::KD, NS = S::NS, NOUT = S::NOUT, HALF = S::HALF;
@@ -328,18 +341,19 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
         uint32_t g = row;
 #pragma unroll
         for (int j = 0; j < K; ++j) g = insert_zero32(g, a.lp[j]);
-        return g;
+        return SW ? swz128(g) : g;
     };
     // offset of group member c (bit j of c at tile bit lp[j]); for the unrolled constant
-    // c this is an OR of the bits 1 << lp[j] held in K registers
+    // c this is an XOR of the (swizzled) bits 1 << lp[j] held in K registers, and a
+    // member's index is group base XOR offset
     uint32_t tbit[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) tbit[j] = 1u << a.lp[j];
+    for (int j = 0; j < K; ++j) tbit[j] = SW ? swz128(1u << a.lp[j]) : 1u << a.lp[j];
     auto member_off = [&](uint32_t c) {
         uint32_t o = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j)
-            if ((c >> j) & 1u) o |= tbit[j];
+            if ((c >> j) & 1u) o ^= tbit[j];
         return o;
     };
 
@@ -386,8 +400,16 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
             __syncwarp();
             if (lane < nseg) {
                 float2 *dst = reinterpret_cast<float2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
-                bulk_g2s(smem_u32(dst + (size_t)lane * seg_amps), psi + tile_base(sl, t) + sl.my_off,
-                         seg_bytes, bar);
+                if constexpr (SW) {
+                    // segment = `boxes` boxes of box_rows 128-byte rows (16 amplitudes each)
+                    const int32_t row0 = (int32_t)((tile_base(sl, t) + sl.my_off) >> 4);
+                    const uint32_t d0 = smem_u32(dst + (size_t)lane * seg_amps);
+                    for (uint32_t bx = 0; bx < a.boxes; ++bx)
+                        tma_load_2d(d0 + bx * a.box_rows * 128u, &a.tmap, 0, row0 + (int32_t)(bx * a.box_rows), bar);
+                } else {
+                    bulk_g2s(smem_u32(dst + (size_t)lane * seg_amps), psi + tile_base(sl, t) + sl.my_off,
+                             seg_bytes, bar);
+                }
             }
         }
     } else if (warp == S::W_MMA) {
@@ -476,7 +498,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
 #pragma unroll
                 for (uint32_t c = 0; c < HALF; ++c) {
                     const uint32_t mo = member_off(part * HALF + c);
-                    v[c] = rs[gbase | (XP ? (mo ^ cx) : mo)];
+                    v[c] = rs[gbase ^ (XP ? (mo ^ cx) : mo)];
                     m = fmaxf(m, fmaxf(fabsf(v[c].x), fabsf(v[c].y)));
                 }
                 max_part[part][row] = m;
@@ -576,7 +598,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
                     }
                     xor_unpermute(o, xl, a.xt);   // o[c] = member c ^ x (x < HALF)
 #pragma unroll
-                    for (uint32_t c = 0; c < HALF; ++c) out[gbase | (member_off(part * HALF + c) ^ cx)] = o[c];
+                    for (uint32_t c = 0; c < HALF; ++c) out[gbase ^ member_off(part * HALF + c) ^ cx] = o[c];
                 } else {
                     // member order: each chunk of eight members is written as soon as it is
                     // formed (fewer live registers than holding the half row)
@@ -589,7 +611,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
                         for (uint32_t i = 0; i < 16; i += 2) {
                             const float re = __fmaf_rn(d12[i], 1.f / 512.f, d0[i]) * osc;
                             const float im = __fmaf_rn(d12[i + 1], 1.f / 512.f, d0[i + 1]) * osc;
-                            out[gbase | member_off(part * HALF + (c0 + i) / 2)] = make_float2(re, im);
+                            out[gbase ^ member_off(part * HALF + (c0 + i) / 2)] = make_float2(re, im);
                         }
                     }
                 }
@@ -600,9 +622,17 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
             }
             if (stop) break;
             if (et < 32) {
-                if (lane < nseg)
-                    bulk_s2g(psi + tile_base(sl, t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
-                             seg_bytes);
+                if (lane < nseg) {
+                    if constexpr (SW) {
+                        const int32_t row0 = (int32_t)((tile_base(sl, t) + sl.my_off) >> 4);
+                        const uint32_t s0 = smem_u32(out + (size_t)lane * seg_amps);
+                        for (uint32_t bx = 0; bx < a.boxes; ++bx)
+                            tma_store_2d(&a.tmap, 0, row0 + (int32_t)(bx * a.box_rows), s0 + bx * a.box_rows * 128u);
+                    } else {
+                        bulk_s2g(psi + tile_base(sl, t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
+                                 seg_bytes);
+                    }
+                }
                 bulk_commit();
             }
         }
@@ -613,6 +643,43 @@ __global__ void __launch_bounds__(576, 1) apply_tc(const __grid_constant__ TcArg
     __syncthreads();
     tc_fence_after();
     if (warp == S::W_MMA) tmem_dealloc(tmem, S::TMEM_COLS);
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// The state as a 2-D tensor of 128-byte rows (32 floats = 16 complex64 amplitudes), boxes of
+// box_rows rows, 128-byte swizzle; a segment of 2^L amplitudes (L >= 4) is `boxes` boxes.
+static sv_status encode_state_map(const sv_state *s, uint32_t L, CUtensorMap *map, uint32_t *box_rows,
+                                  uint32_t *boxes) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return svi::set_error(SV_ERR_CUDA, "tensor-core kernel setup: cuTensorMapEncodeTiled unavailable");
+    const uint32_t seg_rows = 1u << (L - 4);
+    *box_rows = std::min(seg_rows, 256u);
+    *boxes = seg_rows / *box_rows;
+    const cuuint64_t dims[2] = {32, 1ull << (s->n - 4)};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {32, *box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s->buf, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return svi::set_error(SV_ERR_CUDA, "tensor-core kernel setup: cuTensorMapEncodeTiled failed (" +
+                                               std::to_string((int)r) + ")");
+    return SV_OK;
 }
 
 template <int K>
@@ -632,6 +699,9 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
             if (init_err == cudaSuccess)
                 init_err = cudaFuncSetAttribute(apply_tc<K, false, 2>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S2::SMEM);
+            if (init_err == cudaSuccess)
+                init_err = cudaFuncSetAttribute(apply_tc<K, false, 2, false, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S2::SMEM);
         }
     });
     if (init_err != cudaSuccess)
@@ -641,12 +711,21 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     // 8-byte accesses: bank pair = tile bits 0..3; targets there get lane-dependent order
     uint32_t tl = 0;
     while (tl < (uint32_t)K && p.lp[tl] < 4u) ++tl;
-    // width 5 without targets in the bank bits: two subtiles per stage (segments twice as
-    // long, half the per-stage work): all targets high 0.82 -> 0.68 ms at 28 qubits,
-    // contiguous 0.70 -> 0.68; the XOR-order variant is slower that way (0.76 -> 0.83)
-    const bool wide = K == 5 && tl == 0 && s->n >= S2::TB;
-    if (wide) p = make_plan(s->n, K, g.t, S2::TB);
+    // width 5 on states of at least 13 qubits: two subtiles per stage (segments twice as
+    // long, half the per-stage work) with the swizzled tensor-map staging, whatever the
+    // targets (no XOR member order); otherwise one subtile, XOR order for bank-bit targets
+    const bool swz = K == 5 && s->n >= S2::TB;
+    const bool wide = swz;
+    if (wide) {
+        p = make_plan(s->n, K, g.t, S2::TB);
+        tl = 0;
+    }
     TcArgs<K> a;
+    a.box_rows = a.boxes = 0;
+    if (swz) {
+        const sv_status st = encode_state_map(s, p.L, &a.tmap, &a.box_rows, &a.boxes);
+        if (st != SV_OK) return st;
+    }
     // R (real embedding of U) and its fixed-point slices, in FP64 on the host
     double rmax = 0.0;
     for (uint32_t i = 0; i < D * D; ++i)
@@ -680,8 +759,8 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     a.xt = std::min(tl, (uint32_t)K - 1u);   // permute within a worker's half of the members
     const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
     // with eight worker warps per role the permutation costs less than even 2-way conflicts
-    if (wide) {
-        if constexpr (K == 5) apply_tc<K, false, 2><<<grid, S2::THREADS, S2::SMEM, s->stream>>>(a);
+    if (swz) {
+        if constexpr (K == 5) apply_tc<K, false, 2, false, true><<<grid, S2::THREADS, S2::SMEM, s->stream>>>(a);
     } else if (a.xt >= 1) {
         apply_tc<K, true, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     } else {

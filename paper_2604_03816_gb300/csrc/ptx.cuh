@@ -150,6 +150,33 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Global -> shared copy of one box of a 2-D tensor map (tile mode) at coordinates (x, y);
+// completion counted on the mbarrier.  x times the element size must be a multiple of 16
+// bytes; the tensor map lives in kernel parameter space (__grid_constant__).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst_smem, const void *tmap, int32_t x, int32_t y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst_smem), "l"(tmap), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared -> global copy of one box of a 2-D tensor map at (x, y), tracked by the issuing
+// thread's bulk groups.  x, y >= 0.
+__device__ __forceinline__ void tma_store_2d(const void *tmap, int32_t x, int32_t y, uint32_t src_smem) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];"
+                 ::"l"(tmap), "r"(x), "r"(y), "r"(src_smem)
+                 : "memory");
+}
+
+// The 128-byte swizzle of TMA tensor copies, for 8-byte elements at index f of a
+// 1024-byte-aligned shared-memory tile: the 16-byte chunk (index bits 1-3) is XORed with
+// the 128-byte row within the 1024-byte block (index bits 4-6).  It is linear over XOR, so
+// swz(a ^ b) = swz(a) ^ swz(b), and its own inverse.
+__device__ __forceinline__ uint32_t swz128(uint32_t f) {
+    return f ^ ((f >> 3) & 0xEu);
+}
+
 // Tile addressing for the warp that moves a tile: lane i (< 2^h) owns segment i of every
 // tile, whose offset from the tile's base it computes once; the tile base deposits the
 // tile index around the h high target bits.  The high-target positions live in
