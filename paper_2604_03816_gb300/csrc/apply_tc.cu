@@ -660,20 +660,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// The state as a 2-D tensor of 128-byte rows (32 floats = 16 complex64 amplitudes), boxes of
-// box_rows rows, 128-byte swizzle; a segment of 2^L amplitudes (L >= 4) is `boxes` boxes.
-static sv_status encode_state_map(const sv_state *s, uint32_t L, CUtensorMap *map, uint32_t *box_rows,
-                                  uint32_t *boxes) {
+// `amps` complex64 amplitudes at buf as a 2-D tensor of 128-byte rows (32 floats = 16
+// amplitudes), boxes of box_rows rows, 128-byte swizzle; a segment of 2^L amplitudes
+// (L >= 4) is `boxes` boxes.
+static sv_status encode_state_map(void *buf, unsigned long long amps, uint32_t L, CUtensorMap *map,
+                                  uint32_t *box_rows, uint32_t *boxes) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return svi::set_error(SV_ERR_CUDA, "tensor-core kernel setup: cuTensorMapEncodeTiled unavailable");
     const uint32_t seg_rows = 1u << (L - 4);
     *box_rows = std::min(seg_rows, 256u);
     *boxes = seg_rows / *box_rows;
-    const cuuint64_t dims[2] = {32, 1ull << (s->n - 4)};
+    const cuuint64_t dims[2] = {32, amps >> 4};
     const cuuint64_t strides[1] = {128};
     const cuuint32_t box[2] = {32, *box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s->buf, dims, strides, box, estr,
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, buf, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
@@ -723,7 +724,7 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     TcArgs<K> a;
     a.box_rows = a.boxes = 0;
     if (swz) {
-        const sv_status st = encode_state_map(s, p.L, &a.tmap, &a.box_rows, &a.boxes);
+        const sv_status st = encode_state_map(s->buf, 1ull << s->n, p.L, &a.tmap, &a.box_rows, &a.boxes);
         if (st != SV_OK) return st;
     }
     // R (real embedding of U) and its fixed-point slices, in FP64 on the host
@@ -774,20 +775,22 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
 // 12 qubits run as width-5 gates (a width-4 gate widened by an identity qubit, chosen as
 // in widen_gate) with one MMA subtile per stage; each state's B is built on the device
 // from the batch's FP32 matrix table.
-template <bool XP>
+// Batched launches use the swizzled tensor-map staging (SW), like single states.
 static cudaError_t tc_batch_setup() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = cudaFuncSetAttribute(apply_tc<5, XP, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        err = cudaFuncSetAttribute(apply_tc<5, false, 1, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)TcShape<5, 1, true>::SMEM);
     });
     return err;
 }
 
+// Also looks up the tensor-map encoder, so that a launch inside a stream capture finds it.
 cudaError_t tc_batch_prepare() {
-    cudaError_t e = tc_batch_setup<false>();
-    return e == cudaSuccess ? tc_batch_setup<true>() : e;
+    const cudaError_t e = tc_batch_setup();
+    if (e == cudaSuccess && !tensor_map_encoder()) return cudaErrorNotSupported;
+    return e;
 }
 
 sv_status launch_tc_batch(const sv_batch_launch &L) {
@@ -816,9 +819,11 @@ sv_status launch_tc_batch(const sv_batch_launch &L) {
         if (jw < 0) { jw = (int)m; t5[m++] = q; }
     }
     const Plan p = make_plan(L.n, 5, t5, S::TB);
-    uint32_t tl = 0;
-    while (tl < 5u && p.lp[tl] < 4u) ++tl;
     TcArgs<5> a;
+    // the whole batch (states back to back) as one tensor; the swizzle spreads the banks
+    const sv_status st = encode_state_map(L.psi, (unsigned long long)L.states << L.n, p.L, &a.tmap, &a.box_rows,
+                                          &a.boxes);
+    if (st != SV_OK) return st;
     std::memset(a.b, 0, sizeof(a.b));
     a.b_inv_scale = 1.f;
     a.psi = L.psi;
@@ -828,16 +833,15 @@ sv_status launch_tc_batch(const sv_batch_launch &L) {
     a.h = p.h;
     for (int j = 0; j < SV_MAX_K; ++j) a.hi[j] = p.hi[j];
     for (int j = 0; j < 5; ++j) a.lp[j] = p.lp[j];
-    a.xs = 4u - tl;
-    a.xt = std::min(tl, 4u);
+    a.xs = 0;
+    a.xt = 0;
     a.utab = static_cast<const float *>(L.utab);
     a.tiles_per_state = p.ntiles;
     a.n = L.n;
     a.kin = L.k;
     a.jw = jw;
     const unsigned grid = (unsigned)std::min<unsigned long long>(a.ntiles, (unsigned long long)L.num_sms);
-    if (a.xt >= 1) apply_tc<5, true, 1, true><<<grid, S::THREADS, S::SMEM, L.stream>>>(a);
-    else apply_tc<5, false, 1, true><<<grid, S::THREADS, S::SMEM, L.stream>>>(a);
+    apply_tc<5, false, 1, true, true><<<grid, S::THREADS, S::SMEM, L.stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;
 }
