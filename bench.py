@@ -45,14 +45,14 @@ FALLBACK_HBM_GBS = 6800.0
 # as null once those sources hash differently).
 KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
-            "sha256_prefix": "88cf5e1b92fe0f5d", "n": 30,
-            "bytes_per_launch": (1.073862e9 + 1.012122e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,*,*,0> 82.9% of GPU time, all apply kernels "
-                      "97.6% (profiles/fused_pass_grid30q_k5_launches.md)",
-            "traffic_source": "apply_tc<5,0,2> ncu capture at 27q scaled to 30q "
+            "sha256_prefix": "2101b909a1708c08", "n": 30,
+            "bytes_per_launch": (1.073838e9 + 1.012321e9) * 8,
+            "kernel": "fused-gate passes: apply_tc<5,0,2,0,1> 82.4% of GPU time, all apply kernels "
+                      "97.4% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "traffic_source": "apply_tc<5,0,2,0,1> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
-             "sha256_prefix": "7184257e2a53bb42", "n": 30,
+             "sha256_prefix": "ef821cf52ae9d6f7", "n": 30,
              "bytes_per_launch": (2.147548e9 + 2.085445e9) * 8,
              "kernel": "fused-gate passes: apply_tc64<*> 98.1% of GPU time "
                        "(profiles/fused_pass_grid30q_c128_k4_launches.md); bound by the "
