@@ -660,17 +660,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// `amps` complex64 amplitudes at buf as a 2-D tensor of 128-byte rows (32 floats = 16
-// amplitudes), boxes of box_rows rows, 128-byte swizzle; a segment of 2^L amplitudes
-// (L >= 4) is `boxes` boxes.
-static sv_status encode_state_map(void *buf, unsigned long long amps, uint32_t L, CUtensorMap *map,
-                                  uint32_t *box_rows, uint32_t *boxes) {
+// `bytes` bytes at buf as a 2-D tensor of 128-byte rows (32 floats), boxes of box_rows
+// rows, 128-byte swizzle in shared memory; a segment of seg_bytes (a multiple of 128) is
+// `boxes` boxes.
+sv_status encode_rows_map(void *buf, unsigned long long bytes, uint32_t seg_bytes, CUtensorMap *map,
+                          uint32_t *box_rows, uint32_t *boxes) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return svi::set_error(SV_ERR_CUDA, "tensor-core kernel setup: cuTensorMapEncodeTiled unavailable");
-    const uint32_t seg_rows = 1u << (L - 4);
+    const uint32_t seg_rows = seg_bytes / 128u;
     *box_rows = std::min(seg_rows, 256u);
     *boxes = seg_rows / *box_rows;
-    const cuuint64_t dims[2] = {32, amps >> 4};
+    const cuuint64_t dims[2] = {32, bytes / 128u};
     const cuuint64_t strides[1] = {128};
     const cuuint32_t box[2] = {32, *box_rows};
     const cuuint32_t estr[2] = {1, 1};
@@ -724,7 +724,7 @@ sv_status launch_tc_t(sv_state *s, const svi::Gate &g) {
     TcArgs<K> a;
     a.box_rows = a.boxes = 0;
     if (swz) {
-        const sv_status st = encode_state_map(s->buf, 1ull << s->n, p.L, &a.tmap, &a.box_rows, &a.boxes);
+        const sv_status st = encode_rows_map(s->buf, 8ull << s->n, 8u << p.L, &a.tmap, &a.box_rows, &a.boxes);
         if (st != SV_OK) return st;
     }
     // R (real embedding of U) and its fixed-point slices, in FP64 on the host
@@ -821,8 +821,8 @@ sv_status launch_tc_batch(const sv_batch_launch &L) {
     const Plan p = make_plan(L.n, 5, t5, S::TB);
     TcArgs<5> a;
     // the whole batch (states back to back) as one tensor; the swizzle spreads the banks
-    const sv_status st = encode_state_map(L.psi, (unsigned long long)L.states << L.n, p.L, &a.tmap, &a.box_rows,
-                                          &a.boxes);
+    const sv_status st = encode_rows_map(L.psi, (8ull * L.states) << L.n, 8u << p.L, &a.tmap, &a.box_rows,
+                                         &a.boxes);
     if (st != SV_OK) return st;
     std::memset(a.b, 0, sizeof(a.b));
     a.b_inv_scale = 1.f;

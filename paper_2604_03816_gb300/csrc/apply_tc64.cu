@@ -28,6 +28,7 @@
 // double-buffered in TMEM (2 x 96 + 2 x 160 = 512 columns); every wait bounded with a
 // shared abort flag.
 #include <cuda_fp16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -74,6 +75,10 @@ struct Tc64S {
 using Tc64 = Tc64S<1>;
 
 struct Tc64Args {
+    // swizzled launches (SW): the state as a 2-D tensor of 128-byte rows (8 amplitudes),
+    // `boxes` boxes of box_rows rows per segment, 128-byte swizzle in shared memory
+    CUtensorMap tmap;
+    uint32_t box_rows, boxes;
     int16_t b[6][32 * 32];   // digits of R (row-major n x kk), most significant first
     int b_exp;               // max |R| < 2^b_exp
     void *psi;
@@ -142,10 +147,19 @@ __device__ __forceinline__ double combine_levels(float f0, float f1, float f2, f
     return __longlong_as_double(b + ((long long)p << 52));
 }
 
-// XP: the launch has targets among tile bits 0..2 and takes members in the lane's XOR
+// XP (not launched: two bank-bit targets now take the swizzled staging, SW): the launch
+// has targets among tile bits 0..2 and takes members in the lane's XOR
 // order; otherwise no permutation code at all.  The pipelines count tiles (j: raw stage,
 // output staging) and MMA subtiles (js = j SUB + sub: A and D buffers, row exponents).
-template <bool XP, int SUB = 1>
+// 16-byte elements: the 128-byte swizzle XORs the 16-byte chunk (index bits 0-2) with the
+// 128-byte row within each 1 KiB (index bits 3-5); linear over XOR, its own inverse.
+__device__ __forceinline__ uint32_t swz128_16(uint32_t f) { return f ^ ((f >> 3) & 7u); }
+
+// SW: tiles move by 2-D tensor-map copies with the 128-byte swizzle and the roles address
+// them through it, so a warp's lanes reach different banks whatever the targets (no XOR
+// member order: XP = false).  The swizzle is applied to the group base and the target
+// bits, which then combine by XOR.
+template <bool XP, int SUB = 1, bool SW = false>
 __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc64Args a) {
     using S = Tc64S<SUB>;
     constexpr uint32_t KD = S::KD, NS = S::NS, NOUT = S::NOUT;
@@ -206,13 +220,18 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         uint32_t g = row;
 #pragma unroll
         for (int j = 0; j < 4; ++j) g = insert_zero32(g, a.lp[j]);
-        return g;
+        return SW ? swz128_16(g) : g;
     };
-    // offset of group member c (bit j of c at tile position lp[j])
+    // tile offset of target j (swizzled with SW; four registers), and of group member c:
+    // the XOR of the offsets of its set bits; a member's index is group base XOR offset
+    uint32_t tb[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) tb[j] = SW ? swz128_16(1u << a.lp[j]) : 1u << a.lp[j];
     auto member_off = [&](uint32_t c) {
         uint32_t o = 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) o |= ((c >> j) & 1u) << a.lp[j];
+        for (int j = 0; j < 4; ++j)
+            if ((c >> j) & 1u) o ^= tb[j];
         return o;
     };
 
@@ -231,8 +250,16 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
             __syncwarp();
             if (lane < nseg) {
                 double2 *dst = reinterpret_cast<double2 *>(smem + S::OFF_RAW + s * S::TILE_BYTES);
-                bulk_g2s(smem_u32(dst + (size_t)lane * seg_amps), psi + sl.base(t) + sl.my_off,
-                         seg_bytes, bar);
+                if constexpr (SW) {
+                    // segment = `boxes` boxes of box_rows 128-byte rows (8 amplitudes each)
+                    const int32_t row0 = (int32_t)((sl.base(t) + sl.my_off) >> 3);
+                    const uint32_t d0 = smem_u32(dst + (size_t)lane * seg_amps);
+                    for (uint32_t bx = 0; bx < a.boxes; ++bx)
+                        tma_load_2d(d0 + bx * a.box_rows * 128u, &a.tmap, 0, row0 + (int32_t)(bx * a.box_rows), bar);
+                } else {
+                    bulk_g2s(smem_u32(dst + (size_t)lane * seg_amps), psi + sl.base(t) + sl.my_off,
+                             seg_bytes, bar);
+                }
             }
         }
     } else if (warp == S::W_MMA) {
@@ -280,7 +307,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         // the code small (the roles run different code on every SM sub-partition).
         const uint32_t row = (warp & 3u) * 32u + lane;
         const uint32_t part = warp >> 2;
-        const uint32_t lo_off[4] = {0u, 1u << a.lp[0], 1u << a.lp[1], (1u << a.lp[0]) | (1u << a.lp[1])};
+        const uint32_t lo_off[4] = {0u, tb[0], tb[1], tb[0] ^ tb[1]};
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         const uint32_t cx = ((xl & 1u) << a.lp[0]) | (((xl >> 1) & 1u) << a.lp[1]);
         uint32_t j = 0;
@@ -300,7 +327,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
 #pragma unroll
             for (uint32_t c = 0; c < 8; ++c) {
                 const uint32_t *w = reinterpret_cast<const uint32_t *>(
-                    rs + (gbase | (XP ? (member_off(part * 8u + c) ^ cx) : member_off(part * 8u + c))));
+                    rs + (gbase ^ (XP ? (member_off(part * 8u + c) ^ cx) : member_off(part * 8u + c))));
                 em = max(em, max(w[1] & 0x7FFFFFFFu, w[3] & 0x7FFFFFFFu));
             }
             emax_part[part][row] = max(em >> 20, 1u);
@@ -314,12 +341,12 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
             const uint32_t arow = tmem + S::A_COL0 + ab * S::A_SET + (((warp & 3u) * 32u) << 16);
 #pragma unroll 1
             for (uint32_t c0 = part * 8u; c0 < part * 8u + 8u; c0 += 4) {
-                const uint32_t hoff = gbase | (((c0 >> 2) & 1u) << a.lp[2]) | (((c0 >> 3) & 1u) << a.lp[3]);
+                const uint32_t hoff = gbase ^ (((c0 >> 2) & 1u) ? tb[2] : 0u) ^ (((c0 >> 3) & 1u) ? tb[3] : 0u);
                 uint32_t w[6][4];
                 uint4 va[4];
 #pragma unroll
                 for (uint32_t c = 0; c < 4; ++c)
-                    va[c] = *reinterpret_cast<const uint4 *>(rs + (hoff | (XP ? (lo_off[c] ^ cx) : lo_off[c])));
+                    va[c] = *reinterpret_cast<const uint4 *>(rs + (hoff ^ (XP ? (lo_off[c] ^ cx) : lo_off[c])));
                 if constexpr (XP) xor_unpermute4(va, xl, a.xt, sel_u4);
 #pragma unroll
                 for (uint32_t c = 0; c < 4; ++c) {
@@ -352,7 +379,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
         const uint32_t row = quad * 32u + lane;
         const uint32_t et = tid - S::W_EPI * 32u;    // 0..255
         const uint32_t part = et >> 7;
-        const uint32_t lo_off[4] = {0u, 1u << a.lp[0], 1u << a.lp[1], (1u << a.lp[0]) | (1u << a.lp[1])};
+        const uint32_t lo_off[4] = {0u, tb[0], tb[1], tb[0] ^ tb[1]};
         const uint32_t xl = (lane >> a.xs) & ((1u << a.xt) - 1u);
         const uint32_t cx = ((xl & 1u) << a.lp[0]) | (((xl >> 1) & 1u) << a.lp[1]);
         SegLanes sl;
@@ -382,7 +409,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
                 float d[5][8];
                 tmem_ld8x5(lane_addr + c0, KD, d);
                 const uint32_t m0 = c0 >> 1;
-                const uint32_t hoff = gbase | (((m0 >> 2) & 1u) << a.lp[2]) | (((m0 >> 3) & 1u) << a.lp[3]);
+                const uint32_t hoff = gbase ^ (((m0 >> 2) & 1u) ? tb[2] : 0u) ^ (((m0 >> 3) & 1u) ? tb[3] : 0u);
                 double2 o[4];
 #pragma unroll
                 for (uint32_t c = 0; c < 4; ++c) {
@@ -394,7 +421,7 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
                 }
                 if constexpr (XP) xor_unpermute4(o, xl, a.xt, sel_d2);   // o[c] = member c ^ x
 #pragma unroll
-                for (uint32_t c = 0; c < 4; ++c) out[hoff | (XP ? (lo_off[c] ^ cx) : lo_off[c])] = o[c];
+                for (uint32_t c = 0; c < 4; ++c) out[hoff ^ (XP ? (lo_off[c] ^ cx) : lo_off[c])] = o[c];
             }
             tc_fence_before();
             fence_proxy_async_smem();
@@ -403,9 +430,17 @@ __global__ void __launch_bounds__(576, 1) apply_tc64(const __grid_constant__ Tc6
           }
             if (stop) break;
             if (et < 32) {
-                if (lane < nseg)
-                    bulk_s2g(psi + sl.base(t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
-                             seg_bytes);
+                if (lane < nseg) {
+                    if constexpr (SW) {
+                        const int32_t row0 = (int32_t)((sl.base(t) + sl.my_off) >> 3);
+                        const uint32_t s0 = smem_u32(out + (size_t)lane * seg_amps);
+                        for (uint32_t bx = 0; bx < a.boxes; ++bx)
+                            tma_store_2d(&a.tmap, 0, row0 + (int32_t)(bx * a.box_rows), s0 + bx * a.box_rows * 128u);
+                    } else {
+                        bulk_s2g(psi + sl.base(t) + sl.my_off, smem_u32(out + (size_t)lane * seg_amps),
+                                 seg_bytes);
+                    }
+                }
                 bulk_commit();
             }
         }
@@ -427,11 +462,11 @@ sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
         init_err = cudaFuncSetAttribute(apply_tc64<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)S::SMEM);
         if (init_err == cudaSuccess)
-            init_err = cudaFuncSetAttribute(apply_tc64<true, 1>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
-        if (init_err == cudaSuccess)
             init_err = cudaFuncSetAttribute(apply_tc64<false, 2>,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S2::SMEM);
+        if (init_err == cudaSuccess)
+            init_err = cudaFuncSetAttribute(apply_tc64<false, 1, true>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     });
     if (init_err != cudaSuccess)
         return svi::set_error(SV_ERR_CUDA, std::string("tensor-core kernel setup: ") +
@@ -451,13 +486,23 @@ sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
     // (segments of 4 KiB or less), two MMA subtiles per 64 KiB stage: measured at 30
     // qubits, four high targets 11.26 -> 10.58 ms per pass, but two high targets 9.94 ->
     // 10.47 ms, so the mode is kept for the short segments
-    const bool wide = std::min(tl, 2u) < 2u && s->n >= S2::TB && p.h >= 3;
+    // Launches with two targets among the bank bits stage their tiles by tensor-map copies
+    // with the 128-byte swizzle instead of taking the XOR member order (one subtile per
+    // stage); the others keep 1-D bulk copies, where the swizzled staging measured slower.
+    const bool swz = std::min(tl, 2u) >= 2u;
+    const bool wide = !swz && s->n >= S2::TB && p.h >= 3;
     if (wide) {
         p = make_plan(s->n, 4, g->t, S2::TB);
         tl = 0;
         while (tl < 3u && p.lp[tl] < 3u) ++tl;
     }
+    if (swz) tl = 0;
     Tc64Args a;
+    a.box_rows = a.boxes = 0;
+    if (swz) {
+        const sv_status st = encode_rows_map(s->buf, 16ull << s->n, 16u << p.L, &a.tmap, &a.box_rows, &a.boxes);
+        if (st != SV_OK) return st;
+    }
     // R (real embedding of U) and its six digits, exactly, on the host
     double rmax = 0.0;
     for (uint32_t i = 0; i < 256; ++i)
@@ -484,9 +529,10 @@ sv_status launch_tc64(sv_state *s, const svi::Gate &g0) {
     a.xs = 3u - tl;
     a.xt = std::min(tl, 2u);
     const unsigned grid = (unsigned)std::min<unsigned long long>(p.ntiles, (unsigned long long)s->num_sms);
-    // the permutation pays off from two targets in bits 0..2 (4-way conflicts and worse)
-    if (wide && a.xt < 2) apply_tc64<false, 2><<<grid, S2::THREADS, S2::SMEM, s->stream>>>(a);
-    else if (a.xt >= 2) apply_tc64<true, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    // two targets in bits 0..2 (4-way conflicts and worse) take the swizzled staging; one
+    // target there leaves 2-way conflicts, cheaper than either remedy
+    if (swz) apply_tc64<false, 1, true><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
+    else if (wide) apply_tc64<false, 2><<<grid, S2::THREADS, S2::SMEM, s->stream>>>(a);
     else apply_tc64<false, 1><<<grid, S::THREADS, S::SMEM, s->stream>>>(a);
     SV_CUDA(cudaGetLastError());
     return SV_OK;

@@ -138,6 +138,11 @@ struct sv_batch_launch {
 namespace svk {
 cudaError_t tc_batch_prepare();
 sv_status launch_tc_batch(const sv_batch_launch &L);
+// `bytes` bytes at buf as a 2-D tensor of 128-byte rows for TMA tensor copies with the
+// 128-byte shared-memory swizzle; a segment of seg_bytes is *boxes boxes of *box_rows rows
+// (apply_tc.cu).  `map` points to a CUtensorMap.
+sv_status encode_rows_map(void *buf, unsigned long long bytes, uint32_t seg_bytes, struct CUtensorMap_st *map,
+                          uint32_t *box_rows, uint32_t *boxes);
 }  // namespace svk
 
 namespace svi {
