@@ -45,19 +45,19 @@ FALLBACK_HBM_GBS = 6800.0
 # as null once those sources hash differently).
 KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
-            "sha256_prefix": "2101b909a1708c08", "n": 30,
+            "sha256_prefix": "2822291f38aba731", "n": 30,
             "bytes_per_launch": (1.073838e9 + 1.012321e9) * 8,
             "kernel": "fused-gate passes: apply_tc<5,0,2,0,1> 82.4% of GPU time, all apply kernels "
                       "97.4% (profiles/fused_pass_grid30q_k5_launches.md)",
             "traffic_source": "apply_tc<5,0,2,0,1> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
-             "sha256_prefix": "ef821cf52ae9d6f7", "n": 30,
-             "bytes_per_launch": (2.147548e9 + 2.085445e9) * 8,
+             "sha256_prefix": "865b0bd07b9ef27b", "n": 30,
+             "bytes_per_launch": (2.147720e9 + 2.086538e9) * 8,
              "kernel": "fused-gate passes: apply_tc64<*> 98.1% of GPU time "
                        "(profiles/fused_pass_grid30q_c128_k4_launches.md); bound by the "
                        "integer ALU pipe, not HBM (profiles/apply_tc64_c128_27q_ncu.md)",
-             "traffic_source": "apply_tc64<0,*> ncu capture at 27q scaled to 30q "
+             "traffic_source": "apply_tc64<0,2,0> ncu capture at 27q scaled to 30q "
                                "(profiles/apply_tc64_c128_27q_ncu.md)"},
 }
 
