@@ -313,9 +313,10 @@ sv_status sv_topk(sv_state *s, uint32_t k, uint64_t *idx, double *p);
 sv_status sv_gate_structure(const sv_gate *g, uint32_t *kind, uint32_t *control_mask);
 
 /* Kernel selection flags for one state (default 0 = automatic: complex64 gates of width
- * 4 and 5 on states of at least k + 7 qubits run on the tensor cores, complex128 gates of
- * width <= 4 on states of at least 11 qubits too, structured gates on the structure-aware
- * kernels, everything else on the CUDA cores). */
+ * 4 and 5 on states of at least k + 7 qubits, and of any width on states of at least 13
+ * qubits, run on the tensor cores, complex128 gates of width <= 4 on states of at least 11
+ * qubits too, structured gates on the structure-aware kernels, everything else on the CUDA
+ * cores). */
 #define SV_POLICY_NO_TENSOR_CORES 1u   /* always use the CUDA-core kernels */
 #define SV_POLICY_DENSE_ONLY 2u        /* ignore gate structure: every gate a dense pass */
 /* sv_probs into page-locked host memory goes through a device buffer of the probabilities'
