@@ -47,8 +47,8 @@ KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
             "sha256_prefix": "17e4013e3d47450c", "n": 30,
             "bytes_per_launch": (1.073838e9 + 1.012321e9) * 8,
-            "kernel": "fused-gate passes: apply_tc<5,0,2,0,1> 82.4% of GPU time, all apply kernels "
-                      "97.4% (profiles/fused_pass_grid30q_k5_launches.md)",
+            "kernel": "fused-gate passes: apply_tc<5,0,2,0,1> 97.5% of GPU time "
+                      "(profiles/fused_pass_grid30q_k5_launches.md)",
             "traffic_source": "apply_tc<5,0,2,0,1> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
