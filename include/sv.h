@@ -209,7 +209,7 @@ typedef struct {
  * gates commute with it; Eq. 8's DAG has no path between them), so the product is the
  * schedule's.  report->passes counts the HBM passes, report->paired_passes those that
  * applied two gates.  A two-gate pass is bound by instruction issue, not HBM: on GB300 it
- * takes 1.8-1.9x the time of a one-gate pass when the tile is contiguous and more when
+ * takes 1.8-2.2x the time of a one-gate pass when the tile is contiguous and more when
  * it is gathered from short segments, so it is off by default.
  *
  * Precision (Section 5.4).  complex64 states compute in FP32 (tensor-core passes on exact
