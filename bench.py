@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6800.0
 # as null once those sources hash differently).
 KERNELS = {
     "c64": {"files": ("apply_tc.cu", "tc.cuh", "ptx.cuh", "plan.h"),
-            "sha256_prefix": "17e4013e3d47450c", "n": 30,
+            "sha256_prefix": "de4565ba003a3a0c", "n": 30,
             "bytes_per_launch": (1.073838e9 + 1.012321e9) * 8,
             "kernel": "fused-gate passes: apply_tc<5,0,2,0,1> 97.5% of GPU time "
                       "(profiles/fused_pass_grid30q_k5_launches.md)",

@@ -25,8 +25,9 @@
 // below 2^-27 of the row's largest amplitude).
 //
 // One persistent CTA per SM, warp-specialised, every hand-off an mbarrier:
-//   warp 8               TMA producer: lane i issues the 1-D bulk load of segment i of
-//                        each tile into a ring of NS raw stages;
+//   warp 8               TMA producer: lane i issues the load of segment i of each tile
+//                        into a ring of NS raw stages (a 1-D bulk copy, or 2-D tensor-map
+//                        boxes of 128-byte rows with the 128-byte swizzle, SW);
 //   warps 0-7            transform: two warps per TMEM lane quadrant, one group (row of A)
 //                        and half of its members per thread -- gather from the raw stage,
 //                        cut into three 9-bit slices and write them into tensor memory
@@ -37,9 +38,11 @@
 //   warps 10-17          epilogue: two warps per quadrant, tcgen05.ld of half the columns,
 //                        combine, scatter into an output staging tile; warp 10 issues the
 //                        TMA bulk stores.
-// Launches with targets among tile bits 0..3 (where 8-byte accesses pick their bank) take
-// each group's members in a lane-dependent XOR order, undone in registers, so that the
-// lanes of a warp hit different banks.
+// Targets among tile bits 0..3 (where 8-byte accesses pick their bank) would make the
+// lanes of a warp hit one bank.  Width-5 launches on states of 13 qubits or more, and
+// batched launches, avoid that with the swizzled staging (SW); the others (11- and
+// 12-qubit states) take each group's members in a lane-dependent XOR order (XP), undone
+// in registers.
 // So loads, slicing, MMAs and stores of consecutive tiles overlap.  With A in tensor
 // memory, shared memory holds only B, the raw stages and the output staging, so 4 (k = 5)
 // or 8 (k = 4) tiles of loads can be in flight per SM.  Every wait is bounded and any
