@@ -85,3 +85,29 @@ def test_tc_variants_edge_layouts(gpu):
         ref = oracle.run(psi0.astype(np.complex128), OG.gate_list(specs))
         got = _run(sv, n, psi0, sv.gates_from_specs(specs), 0)
         assert np.max(np.abs(got - ref)) <= 1e-5, (n, tg)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_narrow_gates_route_to_the_tensor_cores_from_13_qubits(gpu, k):
+    """complex64 gates narrower than 4 qubits run on the width-5 tensor-core kernel (widened
+    by identity qubits) on states of at least 13 qubits, and on the CUDA cores below; both
+    against the oracle, with targets among the shared-memory bank bits 0-3 included."""
+    sv = gpu
+    import torch
+    rng = np.random.default_rng(9000 + k)
+    for n in (12, 13, 16):
+        for tg in (tuple(range(k)), tuple(range(n - k, n)), (0,) + tuple(range(n - k + 1, n)), None):
+            specs = W.random_unitary_gates(n, 6, k, rng, exact_k=True, targets=tg)
+            psi0 = _state(n, rng)
+            ref = oracle.run(psi0.astype(np.complex128), OG.gate_list(specs))
+            c = sv.sv_fuse(sv.gates_from_specs(specs), n, k)
+            s = sv.sv_alloc(n, 0, stream=torch.cuda.current_stream())
+            sv.sv_set_state(s, psi0)
+            rep = sv.sv_apply_circuit(s, c)
+            got = sv.sv_get_state(s).astype(np.complex128)
+            s.free()
+            assert rep["passes"] >= 1
+            assert rep["tc_passes"] == (rep["passes"] if n >= 13 else 0), (n, tg, rep)
+            assert np.max(np.abs(got - ref)) <= 1e-5, (n, tg)
+            f = abs(np.vdot(ref, got)) ** 2 / np.vdot(got, got).real
+            assert 1 - f <= 1e-6
