@@ -52,8 +52,8 @@ KERNELS = {
             "traffic_source": "apply_tc<5,0,2,0,1> ncu capture at 27q scaled to 30q "
                               "(profiles/apply_tc5_c64_27q_ncu.md)"},
     "c128": {"files": ("apply_tc64.cu", "fixed_point.h", "tc.cuh", "ptx.cuh", "plan.h"),
-             "sha256_prefix": "865b0bd07b9ef27b", "n": 30,
-             "bytes_per_launch": (2.147720e9 + 2.086538e9) * 8,
+             "sha256_prefix": "fe2ac4ee6436bc13", "n": 30,
+             "bytes_per_launch": (2.147647e9 + 2.085257e9) * 8,
              "kernel": "fused-gate passes: apply_tc64<*> 98.1% of GPU time "
                        "(profiles/fused_pass_grid30q_c128_k4_launches.md); bound by the "
                        "integer ALU pipe, not HBM (profiles/apply_tc64_c128_27q_ncu.md)",
